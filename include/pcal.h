@@ -1,0 +1,209 @@
+/*
+ * pcal.h -- C ABI of libpcal, a GB300 (sm_103a) implementation of fast
+ * multi-tone phase-calibration (PCal) signal extraction.
+ *
+ * Method (paper Sec. 2): the baseband stream x[n] carries a comb of N tones
+ * at frequencies i*f_comb + f_offset (Eq. 1).  Rotating by exp(-j*w_offset*n)
+ * (Eq. 3) and folding modulo N_bins = fs/f_comb (Eq. 2) turns the comb into a
+ * pulse P whose DFT gives one complex phasor per tone.  The rotator repeats
+ * every N_rotator = fs/gcd(fs, f_offset) samples (Eq. 4), so the whole
+ * rotate-then-fold is periodic in L = lcm(N_bins, N_rotator) = fs/gcd(fs,
+ * f_comb, f_offset).  libpcal therefore folds FIRST: it keeps exact integer
+ * per-bin statistics of the raw samples over n mod L (2-bit: per-(bin, code)
+ * counts; int8: integer sums; float32: compensated FP32 sums), and rotates,
+ * folds and transforms only the L bins when a result is asked for.
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns PCAL_OK (0) or a negative PCAL_E* code; nothing
+ *     aborts or throws across this boundary.  pcal_strerror() names a code.
+ *   - "device" pointers are CUDA global-memory addresses of the current
+ *     device; "host" pointers are ordinary process memory.  The caller owns
+ *     every buffer it passes in; the plan owns all of its own device state.
+ *   - `stream` is a cudaStream_t passed as an opaque pointer (NULL = the
+ *     legacy default stream).  Asynchronous calls only enqueue work.
+ *   - Sample index n is ABSOLUTE: it counts every sample accumulated into the
+ *     plan since pcal_plan_create, across calls and integration periods, so
+ *     tone phases are referenced to n = 0 of the plan.
+ *   - The tone phasor convention is the raw sum
+ *         T_i = sum_n x[n] * exp(-j*2*pi*(i*f_comb + f_offset)*n/fs),
+ *     i = 0..N-1, forward sign as in Eq. 3, no normalisation.
+ *   - A plan is not thread safe: one host thread drives it at a time.
+ */
+#ifndef PCAL_H
+#define PCAL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define PCAL_OK 0
+#define PCAL_EINVAL (-1)    /* an argument is out of range or inconsistent  */
+#define PCAL_ENOMEM (-2)    /* a device or pinned-host allocation failed    */
+#define PCAL_ECUDA (-3)     /* a CUDA runtime call failed                   */
+#define PCAL_EBUSY (-4)     /* the plan cannot take this call right now     */
+#define PCAL_ETOOLARGE (-5) /* L (or N) exceeds the library's limits        */
+#define PCAL_ETIMEOUT (-6)  /* a bounded device-side wait gave up           */
+
+/* ---- sample formats ---------------------------------------------------- */
+#define PCAL_F32 0  /* real IEEE float32, one sample per 4 bytes            */
+#define PCAL_I8 1   /* two's-complement int8, one sample per byte           */
+#define PCAL_2BIT 2 /* 2-bit codes c = (h<<1)|l, four samples per byte,
+                       sample j of a byte in bits 2j..2j+1 (LSB first);
+                       decoded through a 4-entry level table               */
+
+/* Library limits. */
+#define PCAL_MAX_L 1048576   /* largest combined period L accepted          */
+#define PCAL_MAX_N 8192      /* largest number of tones N accepted          */
+
+/*
+ * Plan geometry (Eq. 4 and N = fs/f_comb from the text after Eq. 1).
+ * Filled by pcal_plan_geometry; all frequencies in integral Hz.
+ */
+typedef struct {
+    int64_t fs, f_comb, f_offset; /* Hz                                      */
+    int64_t N;                    /* tones = N_bins = fs / f_comb            */
+    int64_t N_rot;                /* fs / gcd(fs, f_offset)       (Eq. 4)    */
+    int64_t L;                    /* lcm(N, N_rot) = fs / gcd(fs, fc, fo)    */
+    int64_t step_comb;            /* f_comb / gcd: tone spacing in 2*pi/L    */
+    int64_t step_offset;          /* f_offset / gcd: offset in 2*pi/L        */
+    int32_t format;               /* PCAL_F32, PCAL_I8 or PCAL_2BIT          */
+    int32_t samples_per_byte_x4;  /* 1 (f32), 4 (i8) or 16 (2-bit): samples
+                                     per 4-byte word                         */
+    int64_t row_samples;          /* super-period row of the bulk kernel:
+                                     a multiple of L and of the samples in
+                                     16 bytes, at least 256 bytes long       */
+} pcal_geometry;
+
+/*
+ * pcal_plan_geometry -- validate a plan and compute its periods, on the host
+ * only (no CUDA call).  fs, f_comb, f_offset must be finite, integral Hz with
+ * fs > 0, f_comb > 0, 0 <= f_offset < f_comb and f_comb dividing fs; N must
+ * equal fs/f_comb.  Returns PCAL_EINVAL for a bad argument and
+ * PCAL_ETOOLARGE when L > PCAL_MAX_L or N > PCAL_MAX_N.  `out` (host) is
+ * written only on success.
+ */
+int pcal_plan_geometry(double fs, double f_comb, double f_offset, int N, int sample_format, pcal_geometry* out);
+
+typedef struct pcal_plan pcal_plan;
+
+/*
+ * pcal_plan_create -- make a plan on the current CUDA device (paper Sec. 2,
+ * Eq. 1-4).  Validates exactly like pcal_plan_geometry, then allocates the
+ * plan's device bins (zeroed), its FP64 twiddle table exp(-j*2*pi*m/L),
+ * m < L, and a pinned host result buffer.  On success *out (host) receives
+ * the plan, which the caller releases with pcal_plan_destroy.  The 2-bit
+ * level table defaults to {-3.3359, -1, +1, +3.3359}.  Errors: PCAL_EINVAL,
+ * PCAL_ETOOLARGE, PCAL_ENOMEM, PCAL_ECUDA; on error nothing is allocated.
+ */
+int pcal_plan_create(double fs, double f_comb, double f_offset, int N, int sample_format, pcal_plan** out);
+
+/* pcal_plan_destroy -- synchronise the plan's last stream and free every
+ * resource of the plan.  NULL is accepted. */
+int pcal_plan_destroy(pcal_plan* plan);
+
+/* pcal_plan_get_geometry -- copy the plan's geometry to host memory. */
+int pcal_plan_get_geometry(const pcal_plan* plan, pcal_geometry* out);
+
+/*
+ * pcal_plan_set_levels -- set the values of the 2-bit codes 0..3 (host array
+ * of 4 finite doubles).  Takes effect at the next finalize; the integer
+ * counts are independent of the levels.  PCAL_EINVAL for non-2-bit plans.
+ */
+int pcal_plan_set_levels(pcal_plan* plan, const double levels[4]);
+
+/*
+ * pcal_accumulate -- fold n samples into the plan's bins (Eq. 2 and Eq. 3
+ * combined through the period L of Eq. 4; the fold-first form of Sec. 4.1's
+ * long-accumulator remark).
+ *   samples: DEVICE pointer to n samples in the plan's format, any alignment
+ *            (2-bit: n must be a multiple of 4, i.e. whole bytes).  The caller
+ *            keeps it valid until `stream` has passed this call.
+ *   n:       number of samples, >= 0; 0 is a no-op.
+ *   stream:  cudaStream_t the work is enqueued on; no host synchronisation.
+ * The samples continue the plan's absolute index.  Errors: PCAL_EINVAL (bad
+ * n or NULL pointer with n > 0), PCAL_ECUDA (launch failure).
+ */
+int pcal_accumulate(pcal_plan* plan, const void* samples, int64_t n, void* stream);
+
+/*
+ * pcal_accumulate_host -- as pcal_accumulate, from a HOST buffer.  The
+ * samples are copied to the device through the plan's staging buffers in
+ * chunks that overlap copy and fold; the call returns when the host buffer
+ * may be reused (the fold itself may still be running on `stream`).  Pinned
+ * host memory gives the full copy bandwidth.
+ */
+int pcal_accumulate_host(pcal_plan* plan, const void* host_samples, int64_t n, void* stream);
+
+/*
+ * pcal_finalize_device -- end the current integration period on `stream`
+ * (NULL = the stream of the last accumulate):  decode the bins, rotate each
+ * of the L bins by exp(-j*2*pi*f_offset*k/fs) in FP64 (Eq. 3), fold them to
+ * N bins (Eq. 2), take the N-point DFT (DFT(P), Sec. 2), then amplitude
+ * 2|T_i|/M, phase arg(T_i)+pi/2 (the sin model of Eq. 1), the phase unwrapped
+ * along the comb and the instrumental delay t_d as the |T|^2-weighted
+ * least-squares slope of phase versus tone frequency (phi_i = 2*pi*f_i*t_d,
+ * Eq. 1).  Results stay in the plan's device result buffer (see
+ * pcal_result_device); the bins are reset to zero for the next period and
+ * the absolute sample index keeps counting.  Asynchronous.
+ */
+int pcal_finalize_device(pcal_plan* plan, void* stream);
+
+/*
+ * pcal_finalize -- pcal_finalize_device on the stream of the last
+ * accumulate, then wait for it and copy the N raw phasors T_i to
+ * phasors_out (HOST, 2*N doubles, re/im interleaved).  phasors_out may be
+ * NULL when only the products below are wanted.
+ */
+int pcal_finalize(pcal_plan* plan, double* phasors_out);
+
+/*
+ * pcal_read_results -- wait for the last finalize and copy its results to
+ * host arrays (any of them may be NULL): phasors 2*N (re/im), amp N, phase N
+ * (wrapped to [-pi, pi)), unwrapped N, and td_s / sigma_td_s (seconds).
+ */
+int pcal_read_results(pcal_plan* plan, double* phasors, double* amp, double* phase, double* unwrapped,
+                      double* td_s, double* sigma_td_s);
+
+/* pcal_get_delay -- delay and its 1-sigma of the last finalize (host). */
+int pcal_get_delay(pcal_plan* plan, double* td_s, double* sigma_td_s);
+
+/*
+ * pcal_result_device -- device address of the plan's result buffer, laid out
+ * as doubles: [0,2N) phasors re/im, [2N,3N) amp, [3N,4N) phase, [4N,5N)
+ * unwrapped phase, 5N td, 5N+1 sigma_td, 5N+2 samples integrated.  Owned by
+ * the plan; valid until pcal_plan_destroy.
+ */
+const double* pcal_result_device(const pcal_plan* plan);
+
+/*
+ * pcal_get_bins -- synchronise and copy the bins of the CURRENT integration
+ * period to host memory, exactly:  2-bit: int64 counts[L][4] of each code
+ * per bin; int8: int64 sums[L]; float32: double sums[L] (the compensated
+ * FP32 partial sums combined in FP64).  Bin k holds samples with absolute
+ * index n = k mod L.
+ */
+int pcal_get_bins(pcal_plan* plan, void* host_out);
+
+/* Counters of a plan (host). */
+typedef struct {
+    int64_t n_abs;          /* samples accumulated since plan creation      */
+    int64_t n_period;       /* samples in the current integration period    */
+    int64_t kernel_launches;/* CUDA kernels this plan has launched          */
+    int64_t bulk_launches;  /* of which bulk (TMA bit-plane) fold kernels   */
+    int64_t bytes_folded;   /* sample bytes folded on the device            */
+} pcal_stats;
+
+int pcal_get_stats(const pcal_plan* plan, pcal_stats* out);
+
+/* Static name of a status code. */
+const char* pcal_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PCAL_H */

@@ -1,0 +1,263 @@
+"""Python binding of libpcal: multi-tone phase-calibration extraction on GB300.
+
+Argument marshalling only.  Every step of the extraction runs in libpcal's
+CUDA kernels behind the C ABI declared in include/pcal.h; this module loads
+``_build/libpcal.so`` (built by ``build.build()``) and raises if it is absent.
+Device buffers may be given as torch CUDA tensors or raw device addresses;
+streams as torch streams, raw ``cudaStream_t`` integers or ``None``.
+
+The functions named like the C entry points (``pcal_plan_create`` ...) are
+direct wrappers; :class:`Plan` is the convenience object built on them.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpcal.so")
+
+PCAL_OK, PCAL_EINVAL, PCAL_ENOMEM, PCAL_ECUDA, PCAL_EBUSY, PCAL_ETOOLARGE, PCAL_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+PCAL_F32, PCAL_I8, PCAL_2BIT = 0, 1, 2
+FORMATS = {"f32": PCAL_F32, "i8": PCAL_I8, "2bit": PCAL_2BIT}
+PCAL_MAX_L, PCAL_MAX_N = 1048576, 8192
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [("fs", ctypes.c_int64), ("f_comb", ctypes.c_int64), ("f_offset", ctypes.c_int64),
+                ("N", ctypes.c_int64), ("N_rot", ctypes.c_int64), ("L", ctypes.c_int64),
+                ("step_comb", ctypes.c_int64), ("step_offset", ctypes.c_int64), ("format", ctypes.c_int32),
+                ("samples_per_byte_x4", ctypes.c_int32), ("row_samples", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n_abs", ctypes.c_int64), ("n_period", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("bulk_launches", ctypes.c_int64), ("bytes_folded", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class PcalError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} ({code})")
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libpcal.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"libpcal is not built ({path} missing): run __graft_entry__.build() first")
+    lib = ctypes.CDLL(path)
+    vp, i64, ci, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    P = ctypes.POINTER
+    sig = {
+        "pcal_plan_geometry": ([dbl, dbl, dbl, ci, ci, P(Geometry)], ci),
+        "pcal_plan_create": ([dbl, dbl, dbl, ci, ci, P(vp)], ci),
+        "pcal_plan_destroy": ([vp], ci),
+        "pcal_plan_get_geometry": ([vp, P(Geometry)], ci),
+        "pcal_plan_set_levels": ([vp, P(dbl)], ci),
+        "pcal_accumulate": ([vp, vp, i64, vp], ci),
+        "pcal_accumulate_host": ([vp, vp, i64, vp], ci),
+        "pcal_finalize_device": ([vp, vp], ci),
+        "pcal_finalize": ([vp, vp], ci),
+        "pcal_read_results": ([vp, vp, vp, vp, vp, vp, vp], ci),
+        "pcal_get_delay": ([vp, P(dbl), P(dbl)], ci),
+        "pcal_result_device": ([vp], vp),
+        "pcal_get_bins": ([vp, vp], ci),
+        "pcal_get_stats": ([vp, P(Stats)], ci),
+        "pcal_strerror": ([ci], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def strerror(code: int) -> str:
+    return load().pcal_strerror(int(code)).decode()
+
+
+def _check(rc: int, where: str):
+    if rc != PCAL_OK:
+        raise PcalError(rc, where)
+
+
+def _ptr(x) -> int:
+    """Device address of a torch tensor or an integer address."""
+    if x is None:
+        return 0
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    return int(x)
+
+
+def _stream(s) -> int:
+    if s is None:
+        return 0
+    if hasattr(s, "cuda_stream"):
+        return int(s.cuda_stream)
+    return int(s)
+
+
+# ---- thin wrappers with the C names ------------------------------------------------
+
+def pcal_plan_geometry(fs, f_comb, f_offset, N, sample_format) -> Geometry:
+    g = Geometry()
+    _check(load().pcal_plan_geometry(float(fs), float(f_comb), float(f_offset), int(N), int(sample_format),
+                                     ctypes.byref(g)), "pcal_plan_geometry")
+    return g
+
+
+def pcal_plan_create(fs, f_comb, f_offset, N, sample_format) -> int:
+    h = ctypes.c_void_p()
+    _check(load().pcal_plan_create(float(fs), float(f_comb), float(f_offset), int(N), int(sample_format),
+                                   ctypes.byref(h)), "pcal_plan_create")
+    return h.value
+
+
+def pcal_plan_destroy(plan: int) -> None:
+    _check(load().pcal_plan_destroy(plan), "pcal_plan_destroy")
+
+
+def pcal_plan_set_levels(plan: int, levels) -> None:
+    lv = (ctypes.c_double * 4)(*[float(v) for v in levels])
+    _check(load().pcal_plan_set_levels(plan, lv), "pcal_plan_set_levels")
+
+
+def pcal_accumulate(plan: int, samples, n: int, stream=None) -> None:
+    _check(load().pcal_accumulate(plan, _ptr(samples), int(n), _stream(stream)), "pcal_accumulate")
+
+
+def pcal_accumulate_host(plan: int, host: np.ndarray, n: int, stream=None) -> None:
+    if not host.flags.c_contiguous:
+        raise ValueError("host samples must be C-contiguous")
+    _check(load().pcal_accumulate_host(plan, host.ctypes.data, int(n), _stream(stream)), "pcal_accumulate_host")
+
+
+def pcal_finalize_device(plan: int, stream=None) -> None:
+    _check(load().pcal_finalize_device(plan, _stream(stream)), "pcal_finalize_device")
+
+
+def pcal_finalize(plan: int, n_tones: int) -> np.ndarray:
+    out = np.zeros(2 * n_tones, dtype=np.float64)
+    _check(load().pcal_finalize(plan, out.ctypes.data), "pcal_finalize")
+    return out[0::2] + 1j * out[1::2]
+
+
+def pcal_read_results(plan: int, n_tones: int) -> dict:
+    ph = np.zeros(2 * n_tones)
+    amp, phase, un = np.zeros(n_tones), np.zeros(n_tones), np.zeros(n_tones)
+    td, sg = ctypes.c_double(), ctypes.c_double()
+    _check(load().pcal_read_results(plan, ph.ctypes.data, amp.ctypes.data, phase.ctypes.data, un.ctypes.data,
+                                    ctypes.addressof(td), ctypes.addressof(sg)), "pcal_read_results")
+    return {"phasors": ph[0::2] + 1j * ph[1::2], "amp": amp, "phase": phase, "unwrapped": un, "td": td.value,
+            "sigma_td": sg.value}
+
+
+def pcal_get_delay(plan: int) -> tuple[float, float]:
+    td, sg = ctypes.c_double(), ctypes.c_double()
+    _check(load().pcal_get_delay(plan, ctypes.byref(td), ctypes.byref(sg)), "pcal_get_delay")
+    return td.value, sg.value
+
+
+def pcal_result_device(plan: int) -> int:
+    return int(load().pcal_result_device(plan) or 0)
+
+
+def pcal_get_bins(plan: int, geometry: Geometry) -> np.ndarray:
+    L = int(geometry.L)
+    if geometry.format == PCAL_2BIT:
+        out = np.zeros((L, 4), dtype=np.int64)
+    elif geometry.format == PCAL_I8:
+        out = np.zeros(L, dtype=np.int64)
+    else:
+        out = np.zeros(L, dtype=np.float64)
+    _check(load().pcal_get_bins(plan, out.ctypes.data), "pcal_get_bins")
+    return out
+
+
+def pcal_get_stats(plan: int) -> Stats:
+    s = Stats()
+    _check(load().pcal_get_stats(plan, ctypes.byref(s)), "pcal_get_stats")
+    return s
+
+
+# ---- convenience object ---------------------------------------------------------------
+
+class Plan:
+    """One extraction plan (one baseband channel) on the current CUDA device."""
+
+    def __init__(self, fs: int, f_comb: int, f_offset: int, fmt: str = "2bit", N: int | None = None):
+        N = int(fs) // int(f_comb) if N is None else int(N)
+        self.fmt = fmt
+        self.handle = pcal_plan_create(fs, f_comb, f_offset, N, FORMATS[fmt])
+        g = Geometry()
+        _check(load().pcal_plan_get_geometry(self.handle, ctypes.byref(g)), "pcal_plan_get_geometry")
+        self.geometry = g
+        self.N, self.L = int(g.N), int(g.L)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            pcal_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_levels(self, levels):
+        pcal_plan_set_levels(self.handle, levels)
+
+    def accumulate(self, samples, n: int | None = None, stream=None):
+        """Fold device samples (a torch CUDA tensor of the plan's format, or
+        an address with an explicit n)."""
+        if n is None:
+            n = samples.numel() * (4 if self.fmt == "2bit" else 1)
+        pcal_accumulate(self.handle, samples, n, stream)
+
+    def accumulate_host(self, host: np.ndarray, n: int | None = None, stream=None):
+        if n is None:
+            n = host.size * (4 if self.fmt == "2bit" else 1)
+        pcal_accumulate_host(self.handle, host, n, stream)
+
+    def finalize_device(self, stream=None):
+        pcal_finalize_device(self.handle, stream)
+
+    def finalize(self) -> np.ndarray:
+        return pcal_finalize(self.handle, self.N)
+
+    def results(self) -> dict:
+        return pcal_read_results(self.handle, self.N)
+
+    def bins(self) -> np.ndarray:
+        return pcal_get_bins(self.handle, self.geometry)
+
+    def stats(self) -> dict:
+        return pcal_get_stats(self.handle).as_dict()
+
+    @property
+    def result_device_ptr(self) -> int:
+        return pcal_result_device(self.handle)

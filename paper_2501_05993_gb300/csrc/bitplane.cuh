@@ -1,0 +1,111 @@
+// Bit-sliced counters for the 2-bit fold.
+//
+// A 32-bit word of 2-bit samples holds 16 samples; bit 2j is the l bit and
+// bit 2j+1 the h bit of sample j (code = (h<<1)|l).  A thread that always
+// reads the SAME word position of every row sees the same 16 bins in every
+// word, so it can count, for each of the 32 bit positions, how many of its
+// words have that bit set -- a "positional popcount".  It keeps the counts
+// bit-sliced: plane i holds bit i of all 32 counters, and adding a word is a
+// carry-save (full-adder) operation on whole planes, two 3-input logic ops
+// per full adder for all 32 counters at once.  Words are added 16 at a time
+// through a Harley-Seal tree (15 full adders), whose weight-16 output ripples
+// into the upper planes.
+//
+// The h AND l count of each sample comes from a second stream: for a pair of
+// words (a, b), d = (a & (a>>1) & 0x5555...) | (b & (b<<1) & 0xAAAA...) puts
+// the (h AND l) bit of sample j of word a at bit 2j and that of word b at bit
+// 2j+1, so one word of the second stream counts two input words.
+//
+// At the end the planes are turned into integers by a bit-matrix transpose
+// of 16 planes x 32 positions done as two independent 16x16 transposes (low
+// and high half of each word): afterwards word i holds the count of position
+// i in its low 16 bits and of position i+16 in its high 16 bits.
+#pragma once
+
+#include <stdint.h>
+
+#ifndef PCAL_HD
+#if defined(__CUDACC__)
+#define PCAL_HD __host__ __device__ __forceinline__
+#else
+#define PCAL_HD inline
+#endif
+#endif
+
+namespace pcal_bits {
+
+// Full adder on bit planes: l = a ^ b ^ c, h = majority(a, b, c).
+PCAL_HD void csa(uint32_t& h, uint32_t& l, uint32_t a, uint32_t b, uint32_t c) {
+    const uint32_t u = a ^ b;
+    h = (a & b) | (u & c);
+    l = u ^ c;
+}
+
+// Adds 16 words into (ones, twos, fours, eights); returns the weight-16 carry.
+PCAL_HD uint32_t harley_seal16(const uint32_t* x, uint32_t& ones, uint32_t& twos, uint32_t& fours, uint32_t& eights) {
+    uint32_t tA, tB, fA, fB, eA, eB, s16;
+    csa(tA, ones, ones, x[0], x[1]);
+    csa(tB, ones, ones, x[2], x[3]);
+    csa(fA, twos, twos, tA, tB);
+    csa(tA, ones, ones, x[4], x[5]);
+    csa(tB, ones, ones, x[6], x[7]);
+    csa(fB, twos, twos, tA, tB);
+    csa(eA, fours, fours, fA, fB);
+    csa(tA, ones, ones, x[8], x[9]);
+    csa(tB, ones, ones, x[10], x[11]);
+    csa(fA, twos, twos, tA, tB);
+    csa(tA, ones, ones, x[12], x[13]);
+    csa(tB, ones, ones, x[14], x[15]);
+    csa(fB, twos, twos, tA, tB);
+    csa(eB, fours, fours, fA, fB);
+    csa(s16, eights, eights, eA, eB);
+    return s16;
+}
+
+// Adds 8 words into (ones, twos, fours); returns the weight-8 carry.
+PCAL_HD uint32_t harley_seal8(const uint32_t* x, uint32_t& ones, uint32_t& twos, uint32_t& fours) {
+    uint32_t tA, tB, fA, fB, e8;
+    csa(tA, ones, ones, x[0], x[1]);
+    csa(tB, ones, ones, x[2], x[3]);
+    csa(fA, twos, twos, tA, tB);
+    csa(tA, ones, ones, x[4], x[5]);
+    csa(tB, ones, ones, x[6], x[7]);
+    csa(fB, twos, twos, tA, tB);
+    csa(e8, fours, fours, fA, fB);
+    return e8;
+}
+
+// Ripple-carry increment of a U-plane counter by the 1-bit word x.
+template <int U>
+PCAL_HD void ripple(uint32_t (&up)[U], uint32_t x) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const uint32_t c = up[u] & x;
+        up[u] ^= x;
+        x = c;
+    }
+}
+
+// (h AND l) bits of two words packed into one (see the header comment).
+PCAL_HD uint32_t hl_pair(uint32_t a, uint32_t b) {
+    return (a & (a >> 1) & 0x55555555u) | (b & (b << 1) & 0xAAAAAAAAu);
+}
+
+// In-place transpose of two 16x16 bit matrices held in the low and high
+// halves of A[0..15]: afterwards bit b of A[i] (low half) is the former bit
+// i of A[b], and likewise for the high half with i+16.
+PCAL_HD void transpose16x2(uint32_t (&A)[16]) {
+#pragma unroll
+    for (int j = 8, s = 0; j > 0; j >>= 1, ++s) {
+        const uint32_t m = s == 0 ? 0x00FF00FFu : (s == 1 ? 0x0F0F0F0Fu : (s == 2 ? 0x33333333u : 0x55555555u));
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            if (r & j) continue;
+            const uint32_t t = ((A[r] >> j) ^ A[r + j]) & m;
+            A[r] ^= t << j;
+            A[r + j] ^= t;
+        }
+    }
+}
+
+}  // namespace pcal_bits

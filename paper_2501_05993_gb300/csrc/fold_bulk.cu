@@ -1,0 +1,527 @@
+// Bulk fold kernels of libpcal (paper Sec. 2, Eq. 2 with the period L of
+// Eq. 4, folded before rotating as in Sec. 4.1's long-accumulator remark).
+//
+// Layout.  The body of an accumulate call is viewed as a 2-D array of rows:
+// each row is `row_samples` samples, a whole number of periods L and of
+// 16-byte vectors, so word c of every row always carries the same bins
+// (k_a + spw*c + j) mod L, j < spw (spw = samples per 32-bit word).  The grid
+// tiles this array by (column group, row group): a CTA owns C_w columns of
+// rows_per_cta consecutive rows, and each of its consumer threads owns ONE
+// column (word position) and a fixed subset of the rows (replica q of r takes
+// rows q, q+r, q+2r, ...).  A thread's bins therefore never change, and it
+// keeps its statistics in registers until the end.
+//
+// Movement.  One producer thread streams the CTA's tile through a ring of
+// shared-memory stages with 2-D TMA copies (cp.async.bulk.tensor, tensor map
+// over the rows; rows past the end read as zeros, which add nothing), paced
+// by full/empty mbarriers.  Every wait is bounded: a wait that gives up sets
+// a flag in the plan's device error word and the CTA drains and exits.
+//
+// Arithmetic per format:
+//   2-bit  bit-sliced positional popcounts of the l bits, the h bits and the
+//          (h AND l) bits (bitplane.cuh), about 8 integer ops per 16 samples;
+//   int8   four IDP4A per word into exact 32-bit sums;
+//   f32    Neumaier-compensated FP32 sums.
+// At the end each CTA merges its replicas in shared memory and adds its
+// integer bins to the plan's accumulators with global atomics (order-free,
+// exact); float32 tiles write fixed-order partials that a second kernel sums
+// per bin in a fixed order, so float results are deterministic.
+#include <stdio.h>
+
+#include <cudaTypedefs.h>
+
+#include "bitplane.cuh"
+#include "internal.cuh"
+
+namespace {
+
+constexpr int kMaxBlock = 512;           // consumer threads + producer warp
+constexpr int kSmemBudget = 200 * 1024;  // dynamic shared memory per CTA
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+struct BulkArgs {
+    int cols_total;   // words per row
+    int col_width;    // C_w
+    int col_groups;   // G_c
+    int replicas;     // r
+    int box_rows;     // rows per stage
+    int stages;
+    int consumers;    // C_w * r
+    uint32_t stage_stride;  // bytes between stages (1024-aligned)
+    uint32_t tx_bytes;      // bytes one TMA box delivers
+    int64_t rows_per_cta;
+    int64_t n_rows;
+    int64_t k_a;      // phase of the first sample of row 0
+    int64_t L;
+    unsigned long long* acc2;
+    long long* acc8;
+    float2* partf;    // f32: [row group][cols_total] partial sums
+    unsigned int* err;
+};
+
+// ---- PTX wrappers -------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase of `parity` to complete.
+__device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (uint32_t i = 0; i < kSpinLimit; ++i) {
+        if (mbar_test(bar, parity)) return true;
+        if (i > 64) __nanosleep(i < 4096 ? 32 : 256);
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
+
+
+// ---- per-format consumer state --------------------------------------------------
+
+template <int U>
+struct Acc2 {
+    // w stream: 4 Harley-Seal planes + U upper planes; d stream: 3 + U.
+    uint32_t w1 = 0, w2 = 0, w4 = 0, w8 = 0, wu[U];
+    uint32_t d1 = 0, d2 = 0, d4 = 0, du[U];
+    __device__ Acc2() {
+#pragma unroll
+        for (int u = 0; u < U; ++u) wu[u] = du[u] = 0;
+    }
+    // 16 words of this thread's column, from 16 of its rows.
+    __device__ __forceinline__ void add16(const uint32_t (&x)[16]) {
+        using namespace pcal_bits;
+        uint32_t d[8];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) d[m] = hl_pair(x[2 * m], x[2 * m + 1]);
+        ripple<U>(wu, harley_seal16(x, w1, w2, w4, w8));
+        ripple<U>(du, harley_seal8(d, d1, d2, d4));
+    }
+};
+
+struct Acc8 {
+    int s[4] = {0, 0, 0, 0};
+    __device__ __forceinline__ void add(uint32_t w) {
+        s[0] = __dp4a((int)w, 0x00000001, s[0]);
+        s[1] = __dp4a((int)w, 0x00000100, s[1]);
+        s[2] = __dp4a((int)w, 0x00010000, s[2]);
+        s[3] = __dp4a((int)w, 0x01000000, s[3]);
+    }
+};
+
+struct AccF {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(uint32_t w) {
+        const float x = __uint_as_float(w);
+        const float t = s + x;
+        c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
+        s = t;
+    }
+};
+
+// ---- the kernel ------------------------------------------------------------------
+// FMT: PCAL_2BIT, PCAL_I8 or PCAL_F32.  U: upper bit planes (2-bit only).
+template <int FMT, int U>
+__global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                                 const BulkArgs a) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    const int tid = threadIdx.x;
+    const int n_cons_warps = (a.consumers + 31) / 32;
+    const int producer_warp = n_cons_warps;
+    const int cg = blockIdx.x % a.col_groups;
+    const int64_t rg = blockIdx.x / a.col_groups;
+    const int c0 = cg * a.col_width;
+    const int64_t row0 = rg * a.rows_per_cta;
+    int64_t row_end = row0 + a.rows_per_cta;
+    if (row_end > a.n_rows) row_end = a.n_rows;
+    const int n_boxes = row_end > row0 ? (int)((row_end - row0 + a.box_rows - 1) / a.box_rows) : 0;
+
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)a.stages * a.stage_stride);
+    uint64_t* empty = full + a.stages;
+    uint8_t* merge = reinterpret_cast<uint8_t*>(empty + a.stages);
+    __shared__ int s_failed;
+
+    if (tid == 0) {
+        s_failed = 0;
+        for (int s = 0; s < a.stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], n_cons_warps);
+        }
+        fence_barrier_init();
+    }
+    // zero the merge area
+    {
+        const int words = FMT == PCAL_2BIT ? a.col_width * 32 : (FMT == PCAL_I8 ? a.col_width * 4 : 0);
+        for (int i = tid; i < words; i += blockDim.x) reinterpret_cast<uint32_t*>(merge)[i] = 0;
+    }
+    __syncthreads();
+
+    const int col = tid % a.col_width;
+    const int q = tid / a.col_width;
+    Acc2<(FMT == PCAL_2BIT ? U : 1)> acc2;
+    Acc8 acc8;
+    AccF accf;
+
+    if (tid / 32 == producer_warp) {
+        // ---------------- producer ----------------
+        if (tid % 32 == 0) {
+            int issued = 0;
+            for (int j = 0; j < n_boxes; ++j) {
+                const int s = j % a.stages;
+                const uint32_t use = j / a.stages;
+                if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1)) {
+                    atomicOr(a.err, PCAL_DERR_EMPTY_WAIT);
+                    s_failed = 1;
+                    break;
+                }
+                mbar_arrive_expect_tx(&full[s], a.tx_bytes);
+                tma_load_2d(smem + (size_t)s * a.stage_stride, &tmap, c0, (int)(row0 + (int64_t)j * a.box_rows),
+                            &full[s]);
+                issued = j + 1;
+            }
+            // Drain: the most recent fill of every stage must have landed
+            // before the CTA may exit (its shared memory is then reused).
+            for (int s = 0; s < a.stages && s < issued; ++s) {
+                const int last = s + a.stages * ((issued - 1 - s) / a.stages);
+                if (!mbar_wait(&full[s], (uint32_t)(last / a.stages) & 1)) {
+                    atomicOr(a.err, PCAL_DERR_DRAIN_WAIT);
+                    s_failed = 1;
+                }
+            }
+        }
+    } else {
+        // ---------------- consumers ----------------
+        // Every lane of a consumer warp takes part in the waits and in the
+        // per-warp release; lanes past `consumers` only skip the arithmetic.
+        const bool active = tid < a.consumers;
+        const int rows_per_rep = a.box_rows / a.replicas;
+        for (int j = 0; j < n_boxes; ++j) {
+            const int s = j % a.stages;
+            const uint32_t use = j / a.stages;
+            if (!mbar_wait(&full[s], use & 1)) {
+                atomicOr(a.err, PCAL_DERR_FULL_WAIT);
+                s_failed = 1;
+                break;
+            }
+            const uint32_t* tile = reinterpret_cast<const uint32_t*>(smem + (size_t)s * a.stage_stride);
+            if (active) {
+                if (FMT == PCAL_2BIT) {
+                    for (int b = 0; b < rows_per_rep; b += 16) {
+                        uint32_t x[16];
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) x[i] = tile[(q + a.replicas * (b + i)) * a.col_width + col];
+                        acc2.add16(x);
+                    }
+                } else if (FMT == PCAL_I8) {
+#pragma unroll 4
+                    for (int i = 0; i < rows_per_rep; ++i) acc8.add(tile[(q + a.replicas * i) * a.col_width + col]);
+                } else {
+#pragma unroll 4
+                    for (int i = 0; i < rows_per_rep; ++i) accf.add(tile[(q + a.replicas * i) * a.col_width + col]);
+                }
+            }
+            __syncwarp();
+            if (tid % 32 == 0) mbar_arrive(&empty[s]);
+        }
+    }
+    __syncthreads();
+    if (s_failed) return;
+
+    // ---------------- merge replicas, then flush ----------------
+    const int gcol = c0 + col;
+    if (FMT == PCAL_2BIT) {
+        if (tid < a.consumers) {
+            uint32_t W[16], D[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) W[i] = D[i] = 0;
+            W[0] = acc2.w1;
+            W[1] = acc2.w2;
+            W[2] = acc2.w4;
+            W[3] = acc2.w8;
+            D[0] = acc2.d1;
+            D[1] = acc2.d2;
+            D[2] = acc2.d4;
+#pragma unroll
+            for (int u = 0; u < (FMT == PCAL_2BIT ? U : 1); ++u) {
+                if (4 + u < 16) W[4 + u] = acc2.wu[u];
+                if (3 + u < 16) D[3 + u] = acc2.du[u];
+            }
+            pcal_bits::transpose16x2(W);
+            pcal_bits::transpose16x2(D);
+            uint32_t* m = reinterpret_cast<uint32_t*>(merge) + col * 32;
+            if (a.replicas == 1) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    m[i] = W[i];
+                    m[16 + i] = D[i];
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    atomicAdd(&m[i], W[i]);
+                    atomicAdd(&m[16 + i], D[i]);
+                }
+            }
+        }
+        __syncthreads();
+        const int tasks = a.col_width * 16;
+        for (int t = tid; t < tasks; t += blockDim.x) {
+            const int cl = t >> 4, j = t & 15;
+            const int gc = c0 + cl;
+            if (gc >= a.cols_total) continue;
+            const uint32_t* m = reinterpret_cast<const uint32_t*>(merge) + cl * 32;
+            const int pl = 2 * j, ph = 2 * j + 1;  // bit positions of l and h
+            const uint32_t sl = (m[pl & 15] >> (16 * (pl >> 4))) & 0xFFFFu;
+            const uint32_t sh = (m[ph & 15] >> (16 * (ph >> 4))) & 0xFFFFu;
+            const uint32_t shl = ((m[16 + (pl & 15)] >> (16 * (pl >> 4))) & 0xFFFFu) +
+                                 ((m[16 + (ph & 15)] >> (16 * (ph >> 4))) & 0xFFFFu);
+            if ((sl | sh) == 0) continue;
+            const int64_t bin = (a.k_a + 16 * (int64_t)gc + j) % a.L;
+            atomicAdd(&a.acc2[bin], (unsigned long long)sl | ((unsigned long long)sh << 21) |
+                                         ((unsigned long long)shl << 42));
+        }
+    } else if (FMT == PCAL_I8) {
+        int* m = reinterpret_cast<int*>(merge);
+        if (tid < a.consumers) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (acc8.s[j]) atomicAdd(&m[col * 4 + j], acc8.s[j]);
+        }
+        __syncthreads();
+        for (int t = tid; t < a.col_width * 4; t += blockDim.x) {
+            const int gc = c0 + (t >> 2);
+            if (gc >= a.cols_total || m[t] == 0) continue;
+            const int64_t bin = (a.k_a + 4 * (int64_t)gc + (t & 3)) % a.L;
+            atomicAdd(reinterpret_cast<unsigned long long*>(&a.acc8[bin]), (unsigned long long)(long long)m[t]);
+        }
+    } else {
+        // f32: replicas in a fixed order, then one partial per column per
+        // row group; a second kernel sums the partials per bin.
+        float2* m = reinterpret_cast<float2*>(merge);
+        if (tid < a.consumers) m[q * a.col_width + col] = make_float2(accf.s, accf.c);
+        __syncthreads();
+        if (tid < a.col_width && gcol < a.cols_total) {
+            float s = 0.f, c = 0.f;
+            for (int r = 0; r < a.replicas; ++r) {
+                const float2 v = m[r * a.col_width + tid];
+                const float t = s + v.x;
+                c += (fabsf(s) >= fabsf(v.x) ? (s - t) + v.x : (v.x - t) + s) + v.y;
+                s = t;
+            }
+            a.partf[rg * a.cols_total + gcol] = make_float2(s, c);
+        }
+    }
+}
+
+// f32: bin k = sum over row groups and over the columns that map to k, in a
+// fixed order, added to the plan's FP64 bins.
+__global__ void reduce_f32_kernel(const float2* __restrict__ part, int64_t row_groups, int cols_total, int64_t k_a,
+                                  int64_t L, double* __restrict__ acc) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= L) return;
+    const int64_t c_first = ((k - k_a) % L + L) % L;
+    if (c_first >= cols_total) return;
+    double s = 0.0;
+    for (int64_t rg = 0; rg < row_groups; ++rg)
+        for (int64_t c = c_first; c < cols_total; c += L) {
+            const float2 v = part[rg * cols_total + c];
+            s += (double)v.x + (double)v.y;
+        }
+    acc[k] += s;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+int bits_for(int64_t v) {
+    int b = 0;
+    while (((int64_t)1 << b) <= v) ++b;
+    return b;
+}
+
+template <int FMT, int U>
+cudaError_t launch_one(const CUtensorMap& map, const BulkArgs& a, int grid, int block, size_t smem, cudaStream_t s) {
+    auto k = bulk_fold_kernel<FMT, U>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, block, smem, s>>>(map, a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int bulk_tiling(const pcal_plan* p, int64_t n_rows, BulkTiling* t) {
+    const int spw = p->g.samples_per_byte_x4;
+    const int cols = (int)(p->g.row_samples / spw);
+    BulkTiling z{};
+    z.cols_total = cols;
+    int gc = (cols + 255) / 256;
+    int cw = (cols + gc - 1) / gc;
+    cw = (cw + 7) / 8 * 8;
+    if (cw > 256) cw = 256;
+    gc = (cols + cw - 1) / cw;
+    z.col_width = cw;
+    z.col_groups = gc;
+    int r = (kMaxBlock - 32) / cw;
+    if (r > 8) r = 8;
+    if (r < 1) r = 1;
+    z.replicas = r;
+    // a stage of about 24 KB, rows a multiple of 16*r (2-bit blocks of 16)
+    const int unit = (p->g.format == PCAL_2BIT ? 16 : 1) * r;
+    int units = (24 * 1024) / (unit * cw * 4);
+    if (units < 1) units = 1;
+    int box = unit * units;
+    while (box > 256) box -= unit;
+    if (box < unit) return -1;
+    z.box_rows = box;
+    const size_t stage = (size_t)box * cw * 4;
+    const size_t stage_al = (stage + 1023) / 1024 * 1024;
+    size_t merge = p->g.format == PCAL_2BIT ? (size_t)cw * 128 : (p->g.format == PCAL_I8 ? (size_t)cw * 16
+                                                                                          : (size_t)cw * r * 8);
+    int stages = (int)((kSmemBudget - merge - 1024) / stage_al);
+    if (stages > 8) stages = 8;
+    if (stages < 2) return -1;
+    z.stages = stages;
+    // row groups: one wave over the SMs, rows per CTA a multiple of the box
+    // and small enough for 16-bit per-CTA counts
+    int64_t gr = p->num_sms / gc;
+    if (gr < 1) gr = 1;
+    int64_t per = (n_rows + gr - 1) / gr;
+    per = (per + box - 1) / box * box;
+    const int64_t max_per = (65535 / box) * box;
+    if (per > max_per) per = max_per;
+    gr = (n_rows + per - 1) / per;
+    z.row_groups = gr;
+    z.rows_per_cta = per;
+    z.upper_planes = 0;
+    if (p->g.format == PCAL_2BIT) {
+        const int64_t blocks = per / r / 16;
+        z.upper_planes = bits_for(blocks);
+    }
+    z.threads = ((cw * r + 31) / 32 + 1) * 32;
+    z.smem_bytes = (size_t)stages * stage_al + 16 * (size_t)stages + merge;
+    *t = z;
+    return 0;
+}
+
+cudaError_t launch_bulk(pcal_plan* p, const void* d_rows, int64_t n_rows, int64_t k_a, cudaStream_t s, int* launched) {
+    *launched = 0;
+    BulkTiling t;
+    if (bulk_tiling(p, n_rows, &t) != 0) return cudaErrorInvalidConfiguration;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
+    if (!enc) return cudaErrorNotSupported;
+    const int spw = p->g.samples_per_byte_x4;
+    CUtensorMap map;
+    cuuint64_t dims[2] = {(cuuint64_t)t.cols_total, (cuuint64_t)n_rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(p->g.row_samples / spw * 4)};
+    cuuint32_t box[2] = {(cuuint32_t)t.col_width, (cuuint32_t)t.box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<void*>(d_rows), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    BulkArgs a{};
+    a.cols_total = t.cols_total;
+    a.col_width = t.col_width;
+    a.col_groups = t.col_groups;
+    a.replicas = t.replicas;
+    a.box_rows = t.box_rows;
+    a.stages = t.stages;
+    a.consumers = t.col_width * t.replicas;
+    a.tx_bytes = (uint32_t)((size_t)t.box_rows * t.col_width * 4);
+    a.stage_stride = (a.tx_bytes + 1023u) / 1024u * 1024u;
+    a.rows_per_cta = t.rows_per_cta;
+    a.n_rows = n_rows;
+    a.k_a = k_a;
+    a.L = p->g.L;
+    a.acc2 = p->d_acc2;
+    a.acc8 = p->d_acc8;
+    a.err = p->d_err;
+    const int grid = (int)(t.col_groups * t.row_groups);
+    cudaError_t e;
+    if (p->g.format == PCAL_F32) {
+        const size_t need = (size_t)t.row_groups * t.cols_total;
+        if (need > p->partf_cap) {
+            cudaFree(p->d_partf);
+            p->d_partf = nullptr;
+            p->partf_cap = 0;
+            e = cudaMalloc(&p->d_partf, need * sizeof(float2));
+            if (e != cudaSuccess) return e;
+            p->partf_cap = need;
+        }
+        a.partf = p->d_partf;
+        e = launch_one<PCAL_F32, 1>(map, a, grid, t.threads, t.smem_bytes, s);
+        if (e != cudaSuccess) return e;
+        reduce_f32_kernel<<<(unsigned)((p->g.L + 255) / 256), 256, 0, s>>>(p->d_partf, t.row_groups, t.cols_total,
+                                                                           k_a, p->g.L, p->d_accf);
+        *launched = 2;
+        p->stats.kernel_launches += 2;
+        return cudaGetLastError();
+    }
+    if (p->g.format == PCAL_I8) {
+        e = launch_one<PCAL_I8, 1>(map, a, grid, t.threads, t.smem_bytes, s);
+    } else {
+        const int u = t.upper_planes;
+        if (u <= 2)
+            e = launch_one<PCAL_2BIT, 2>(map, a, grid, t.threads, t.smem_bytes, s);
+        else if (u <= 4)
+            e = launch_one<PCAL_2BIT, 4>(map, a, grid, t.threads, t.smem_bytes, s);
+        else if (u <= 6)
+            e = launch_one<PCAL_2BIT, 6>(map, a, grid, t.threads, t.smem_bytes, s);
+        else if (u <= 8)
+            e = launch_one<PCAL_2BIT, 8>(map, a, grid, t.threads, t.smem_bytes, s);
+        else if (u <= 10)
+            e = launch_one<PCAL_2BIT, 10>(map, a, grid, t.threads, t.smem_bytes, s);
+        else
+            e = launch_one<PCAL_2BIT, 12>(map, a, grid, t.threads, t.smem_bytes, s);
+    }
+    if (e == cudaSuccess) {
+        *launched = 1;
+        p->stats.kernel_launches += 1;
+    }
+    return e;
+}

@@ -1,0 +1,130 @@
+// Ragged-edge fold kernels of libpcal and the small bookkeeping kernels.
+//
+// The ragged kernels fold any run of samples at any alignment straight into
+// the plan's bins (Eq. 2 with the period L of Eq. 4).  They handle the head
+// before the first 16-byte boundary, the tail after the last whole bulk row,
+// and inputs too short for the bulk kernel.  2-bit and int8 bins are exact
+// integers, so atomic order does not matter; float32 bins are summed by one
+// thread per bin in sample order, so they are deterministic.
+#include "internal.cuh"
+
+namespace {
+
+__global__ void ragged_2bit_kernel(const uint8_t* __restrict__ bytes, int64_t n_bytes, int64_t k0, int64_t L,
+                                   unsigned long long* __restrict__ acc) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_bytes;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t b = bytes[i];
+        if (b == 0) continue;
+        int64_t k = (k0 + 4 * i) % L;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            uint32_t c = (b >> (2 * j)) & 3u;
+            if (c) {
+                unsigned long long l = c & 1u, h = c >> 1;
+                atomicAdd(&acc[k], l | (h << 21) | ((l & h) << 42));
+            }
+            if (++k == L) k = 0;
+        }
+    }
+}
+
+__global__ void ragged_i8_kernel(const int8_t* __restrict__ x, int64_t n, int64_t k0, int64_t L,
+                                 long long* __restrict__ acc) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int v = x[i];
+        if (v) atomicAdd(reinterpret_cast<unsigned long long*>(&acc[(k0 + i) % L]), (unsigned long long)(long long)v);
+    }
+}
+
+// One thread per bin k: sums the samples of this run that fall into bin k, in
+// order, and adds the sum to the plan's FP64 bin.
+__global__ void ragged_f32_kernel(const float* __restrict__ x, int64_t n, int64_t k0, int64_t L,
+                                  double* __restrict__ acc) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= L) return;
+    int64_t t = (k - k0 % L + L) % L;  // first sample index of this run in bin k
+    double s = 0.0;
+    for (; t < n; t += L) s += (double)x[t];
+    if (s != 0.0) acc[k] += s;
+}
+
+// Move the packed 21-bit fields into the wide 64-bit arrays and clear them.
+__global__ void spill2_kernel(unsigned long long* __restrict__ acc, unsigned long long* __restrict__ wide,
+                              int64_t L) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < L; k += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long v = acc[k];
+        if (v) {
+            wide[k] += v & PCAL_F21_MASK;
+            wide[L + k] += (v >> 21) & PCAL_F21_MASK;
+            wide[2 * L + k] += (v >> 42) & PCAL_F21_MASK;
+            acc[k] = 0;
+        }
+    }
+}
+
+// Exact per-(bin, code) counts of the current period: [L][4] int64.
+__global__ void export2_kernel(const unsigned long long* __restrict__ acc, const unsigned long long* __restrict__ wide,
+                               int64_t L, int64_t q, int64_t rem, int64_t a0, long long* __restrict__ out) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < L; k += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long v = acc[k];
+        long long sl = (long long)((v & PCAL_F21_MASK) + wide[k]);
+        long long sh = (long long)(((v >> 21) & PCAL_F21_MASK) + wide[L + k]);
+        long long shl = (long long)(((v >> 42) & PCAL_F21_MASK) + wide[2 * L + k]);
+        int64_t r = (k - a0 + L) % L;
+        long long cnt = q + (r < rem ? 1 : 0);
+        out[4 * k + 3] = shl;
+        out[4 * k + 2] = sh - shl;
+        out[4 * k + 1] = sl - shl;
+        out[4 * k + 0] = cnt - sl - sh + shl;
+    }
+}
+
+inline int grid_for(int64_t work, int threads, int num_sms) {
+    int64_t g = (work + threads - 1) / threads;
+    int64_t cap = (int64_t)num_sms * 8;
+    if (g > cap) g = cap;
+    return g < 1 ? 1 : (int)g;
+}
+
+}  // namespace
+
+cudaError_t launch_ragged(pcal_plan* p, const uint8_t* d_bytes, int64_t n, int64_t k0, cudaStream_t s) {
+    const int64_t L = p->g.L;
+    if (n <= 0) return cudaSuccess;
+    switch (p->g.format) {
+        case PCAL_2BIT: {
+            int64_t nb = n / 4;
+            ragged_2bit_kernel<<<grid_for(nb, 256, p->num_sms), 256, 0, s>>>(d_bytes, nb, k0, L, p->d_acc2);
+            break;
+        }
+        case PCAL_I8:
+            ragged_i8_kernel<<<grid_for(n, 256, p->num_sms), 256, 0, s>>>(reinterpret_cast<const int8_t*>(d_bytes),
+                                                                            n, k0, L, p->d_acc8);
+            break;
+        default: {
+            int64_t g = (L + 255) / 256;
+            ragged_f32_kernel<<<(unsigned)g, 256, 0, s>>>(reinterpret_cast<const float*>(d_bytes), n, k0, L,
+                                                          p->d_accf);
+            break;
+        }
+    }
+    p->stats.kernel_launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spill2(pcal_plan* p, cudaStream_t s) {
+    spill2_kernel<<<grid_for(p->g.L, 256, p->num_sms), 256, 0, s>>>(p->d_acc2, p->d_wide2, p->g.L);
+    p->stats.kernel_launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export_bins(pcal_plan* p, void* d_out, cudaStream_t s) {
+    const int64_t L = p->g.L;
+    const int64_t n_tot = p->n_abs - p->period_start;
+    export2_kernel<<<grid_for(L, 256, p->num_sms), 256, 0, s>>>(p->d_acc2, p->d_wide2, L, n_tot / L, n_tot % L,
+                                                                  p->period_start % L,
+                                                                  reinterpret_cast<long long*>(d_out));
+    p->stats.kernel_launches += 1;
+    return cudaGetLastError();
+}

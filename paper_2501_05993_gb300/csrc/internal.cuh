@@ -1,0 +1,88 @@
+// Internal declarations of libpcal (not part of the C ABI).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pcal.h"
+
+// 2-bit bins are accumulated as one 64-bit word per bin holding three 21-bit
+// fields:  bits 0..20 = sum of l bits, 21..41 = sum of h bits, 42..62 = sum
+// of (h AND l).  Together with the known number of samples per bin these give
+// the exact counts of all four codes.  The host spills the packed words into
+// three wide 64-bit arrays before any field could reach 2^21.
+#define PCAL_F21_MASK 0x1FFFFFull
+#define PCAL_F21_LIMIT ((1ll << 21) - 1)
+
+// Device-side error flags (bitwise OR into pcal_plan::d_err).
+#define PCAL_DERR_FULL_WAIT 1u   // a consumer gave up waiting for a tile
+#define PCAL_DERR_EMPTY_WAIT 2u  // the producer gave up waiting for a slot
+#define PCAL_DERR_DRAIN_WAIT 4u  // a CTA gave up draining its copies
+
+struct pcal_plan {
+    pcal_geometry g;
+    double levels[4];
+    int device;
+    int num_sms;
+    // stream state
+    cudaStream_t last_stream;
+    int64_t n_abs;        // samples accumulated since creation
+    int64_t period_start; // absolute index of the first sample of this period
+    int64_t since_spill;  // 2-bit: samples added since the last spill
+    // device state
+    unsigned long long* d_acc2;   // 2-bit packed counts [L]
+    unsigned long long* d_wide2;  // 2-bit spilled counts [3][L]
+    long long* d_acc8;            // int8 sums [L]
+    double* d_accf;               // float32 sums (FP64) [L]
+    float2* d_partf;              // float32 per-tile partial sums (scratch)
+    size_t partf_cap;             // capacity of d_partf in float2
+    double2* d_tw;                // exp(-j 2 pi m / L), m < L
+    float2* d_twN;                // exp(-j 2 pi m / N), m < N (FP32)
+    double2* d_P;                 // folded rotated bins P[b], b < N (scratch)
+    double2* d_T;                 // tone phasors (scratch before products)
+    double* d_res;                // results, 5N+3 doubles
+    unsigned int* d_ticket;       // [0] fold ticket, [1] dft ticket
+    unsigned int* d_err;          // device error flags
+    // host
+    double* h_res;                // pinned copy of d_res
+    void* h_stage[2];             // pinned staging for pcal_accumulate_host
+    void* d_stage[2];             // device staging for pcal_accumulate_host
+    size_t stage_bytes;
+    cudaEvent_t stage_ev[2];      // fold of staging buffer i finished
+    cudaEvent_t copied_ev[2];     // copy into staging buffer i finished
+    cudaStream_t copy_stream;     // H2D copies of pcal_accumulate_host
+    bool results_valid;
+    pcal_stats stats;
+};
+
+// ---- launchers (return a cudaError_t of the launch) -------------------------
+cudaError_t launch_init_twiddles(pcal_plan* p, cudaStream_t s);
+cudaError_t launch_ragged(pcal_plan* p, const uint8_t* d_bytes, int64_t n_samples, int64_t k0, cudaStream_t s);
+cudaError_t launch_spill2(pcal_plan* p, cudaStream_t s);
+cudaError_t launch_export_bins(pcal_plan* p, void* d_out, cudaStream_t s);
+cudaError_t launch_finalize(pcal_plan* p, cudaStream_t s);
+
+// Bulk fold of whole rows of row_samples samples starting at a 16-byte
+// aligned device address whose first sample has phase k_a = n mod L.
+// Returns cudaSuccess and sets *launched = the number of kernels launched,
+// or an error.  Rows must be >= 1.
+cudaError_t launch_bulk(pcal_plan* p, const void* d_rows, int64_t n_rows, int64_t k_a, cudaStream_t s,
+                        int* launched);
+
+// Tile plan of the bulk kernel for a given plan and row count (host only),
+// exposed so that tests can check the work split.
+struct BulkTiling {
+    int cols_total;    // words per row
+    int col_width;     // words per column group (tile width)
+    int col_groups;    // G_c
+    int replicas;      // consumer threads per column
+    int box_rows;      // rows per TMA box (stage)
+    int stages;        // pipeline depth
+    int64_t row_groups;      // G_r
+    int64_t rows_per_cta;    // multiple of box_rows
+    int upper_planes;  // 2-bit: bit planes above the Harley-Seal tree
+    int threads;       // consumer threads + 1 producer warp
+    size_t smem_bytes;
+};
+int bulk_tiling(const pcal_plan* p, int64_t n_rows, BulkTiling* t);

@@ -1,0 +1,106 @@
+"""The C ABI without a GPU: the library loads, exports every entry point the
+header declares, validates plans on the host, and fails cleanly without a
+device.  Also the host check of the 2-bit kernel's bit-sliced arithmetic."""
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_2501_05993_gb300 as pcal
+from paper_2501_05993_gb300 import build as libbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pcal.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    libbuild.build()
+    return pcal.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pcal_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_core_entry_points():
+    names = declared_functions()
+    for core in ("pcal_plan_create", "pcal_accumulate", "pcal_finalize"):
+        assert core in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", pcal.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (pcal_\w+)", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, f"declared but not exported: {missing}"
+
+
+@pytest.mark.parametrize("fs,fc,fo,fmt,N,L", [
+    (16e6, 1e6, 10e3, pcal.PCAL_F32, 16, 1600),
+    (64e6, 1e6, 10e3, pcal.PCAL_2BIT, 64, 6400),
+    (1024e6, 1e6, 10e3, pcal.PCAL_I8, 1024, 102400),
+    (32e6, 1e6, 0, pcal.PCAL_2BIT, 32, 32),
+    (16, 4, 1, pcal.PCAL_2BIT, 4, 16),
+    (48e6, 1e6, 30e3, pcal.PCAL_I8, 48, 4800),
+])
+def test_geometry(lib, fs, fc, fo, fmt, N, L):
+    g = pcal.pcal_plan_geometry(fs, fc, fo, N, fmt)
+    assert (g.N, g.L) == (N, L)
+    assert g.N_rot == int(fs) // __import__("math").gcd(int(fs), int(fo))
+    spw = {pcal.PCAL_F32: 1, pcal.PCAL_I8: 4, pcal.PCAL_2BIT: 16}[fmt]
+    assert g.samples_per_byte_x4 == spw
+    row_bytes = g.row_samples * 4 // spw
+    assert g.row_samples % L == 0 and g.row_samples % (4 * spw) == 0 and row_bytes >= 256
+
+
+@pytest.mark.parametrize("args,code", [
+    ((16e6, 1e6, 10e3, 15, pcal.PCAL_F32), pcal.PCAL_EINVAL),      # N != fs/fc
+    ((16e6, 1e6, 1e6, 16, pcal.PCAL_F32), pcal.PCAL_EINVAL),       # f_offset >= f_comb
+    ((16e6 + 0.5, 1e6, 10e3, 16, pcal.PCAL_F32), pcal.PCAL_EINVAL),  # non-integral Hz
+    ((16e6, 1e6, -1.0, 16, pcal.PCAL_F32), pcal.PCAL_EINVAL),
+    ((16e6, 3e6, 10e3, 5, pcal.PCAL_F32), pcal.PCAL_EINVAL),       # f_comb does not divide fs
+    ((16e6, 1e6, 10e3, 16, 7), pcal.PCAL_EINVAL),                  # unknown format
+    ((1024e6, 1e6, 7.0, 1024, pcal.PCAL_I8), pcal.PCAL_ETOOLARGE),  # L = fs / gcd = 1.024e9
+    ((16384e6, 1e6, 0.0, 16384, pcal.PCAL_I8), pcal.PCAL_ETOOLARGE),  # N above the cap
+])
+def test_geometry_errors(lib, args, code):
+    with pytest.raises(pcal.PcalError) as ei:
+        pcal.pcal_plan_geometry(*args)
+    assert ei.value.code == code
+
+
+def test_strerror(lib):
+    for code in (0, -1, -2, -3, -4, -5, -6):
+        assert pcal.strerror(code) and pcal.strerror(code) != "unknown pcal status"
+    assert pcal.strerror(-99) == "unknown pcal status"
+
+
+def test_plan_create_without_a_device_fails_cleanly(lib):
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(pcal.PcalError) as ei:
+        pcal.pcal_plan_create(64e6, 1e6, 10e3, 64, pcal.PCAL_2BIT)
+    assert ei.value.code in (pcal.PCAL_ECUDA, pcal.PCAL_ENOMEM)
+
+
+def test_null_arguments_are_rejected(lib):
+    assert lib.pcal_accumulate(None, None, 4, None) == pcal.PCAL_EINVAL
+    assert lib.pcal_finalize(None, None) == pcal.PCAL_EINVAL
+    assert lib.pcal_plan_destroy(None) == pcal.PCAL_OK
+    assert lib.pcal_get_bins(None, None) == pcal.PCAL_EINVAL
+
+
+def test_bitplane_arithmetic_on_host(tmp_path):
+    exe = tmp_path / "bitplane_check"
+    src = os.path.join(ROOT, "tests", "host", "bitplane_check.cpp")
+    inc = os.path.join(ROOT, "paper_2501_05993_gb300", "csrc")
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-I", inc, src, "-o", str(exe)])
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert r.stdout.strip().endswith("OK")
