@@ -168,9 +168,12 @@ def test_two_bit_levels_and_spill(pcal):
 
 
 def test_products_and_delay(pcal):
+    # A weak comb (0.005 sigma): 2-bit quantisation of a strong comb biases
+    # the delay through intermodulation (about -49 ps at 0.01 sigma), which
+    # is a property of the data, not of the extraction.
     fs, fc, fo, td = 64_000_000, 1_000_000, 10_000, 12.5e-9
     n = 4 * 16_000_000
-    host = synth.Stream(fs=fs, fc=fc, fo=fo, amp=0.05, td=td, seed=21).bits2(0, n)
+    host = synth.Stream(fs=fs, fc=fc, fo=fo, amp=0.005, td=td, seed=21).bits2(0, n)
     with pcal.Plan(fs, fc, fo, "2bit") as p:
         keep, addr = to_dev(host)
         p.accumulate(addr, n)
@@ -239,7 +242,7 @@ def test_full_size_two_bit_bench_workload(pcal):
     check_phasors(T, ref)
     pr = oracle.products(ref, n, fs, fc, fo)
     assert abs(r["td"] - pr["td"]) <= 1e-3 * pr["sigma_td"]
-    assert abs(pr["td"] - td) < 5 * pr["sigma_td"]
+    assert abs(r["sigma_td"] - pr["sigma_td"]) <= 1e-3 * pr["sigma_td"]
 
 
 def test_full_size_f32_c1(pcal):
@@ -255,3 +258,4 @@ def test_full_size_f32_c1(pcal):
     check_phasors(T, ref)
     pr = oracle.products(ref, n, fs, fc, fo)
     assert abs(r["td"] - pr["td"]) <= 1e-3 * pr["sigma_td"]
+    assert abs(r["td"] - td) < 5 * pr["sigma_td"]  # unquantised data: no bias
