@@ -79,6 +79,8 @@ int accumulate_run(pcal_plan* p, const uint8_t* d, int64_t n, cudaStream_t s) {
     const int64_t row = p->g.row_samples;
     int64_t rows = (n - head) / row;
     if (bytes_of(p, rows * row) < kBulkMinBytes) rows = 0;
+    BulkTiling probe;
+    if (rows > 0 && bulk_tiling(p, rows, &probe) != 0) rows = 0;  // no tile plan: ragged only
     cudaError_t e = cudaSuccess;
     if (rows == 0) {
         e = launch_ragged(p, d, n, k0, s);

@@ -34,11 +34,31 @@
 
 namespace pcal_bits {
 
+// Three-input logic op: one LOP3 on the device (lut over a=0xF0, b=0xCC,
+// c=0xAA), the plain expression on the host.
+template <int LUT>
+PCAL_HD uint32_t lop3(uint32_t a, uint32_t b, uint32_t c) {
+#if defined(__CUDA_ARCH__)
+    uint32_t d;
+    asm("lop3.b32 %0, %1, %2, %3, %4;" : "=r"(d) : "r"(a), "r"(b), "r"(c), "n"(LUT));
+    return d;
+#else
+    uint32_t d = 0;
+    for (int bit = 0; bit < 32; ++bit) {
+        const int idx = (((a >> bit) & 1) << 2) | (((b >> bit) & 1) << 1) | ((c >> bit) & 1);
+        d |= (uint32_t)((LUT >> idx) & 1) << bit;
+    }
+    return d;
+#endif
+}
+constexpr int kXor3 = 0x96;  // a ^ b ^ c
+constexpr int kMaj3 = 0xE8;  // majority(a, b, c)
+
 // Full adder on bit planes: l = a ^ b ^ c, h = majority(a, b, c).
 PCAL_HD void csa(uint32_t& h, uint32_t& l, uint32_t a, uint32_t b, uint32_t c) {
-    const uint32_t u = a ^ b;
-    h = (a & b) | (u & c);
-    l = u ^ c;
+    const uint32_t hh = lop3<kMaj3>(a, b, c);
+    l = lop3<kXor3>(a, b, c);
+    h = hh;
 }
 
 // Adds 16 words into (ones, twos, fours, eights); returns the weight-16 carry.
@@ -88,7 +108,27 @@ PCAL_HD void ripple(uint32_t (&up)[U], uint32_t x) {
 
 // (h AND l) bits of two words packed into one (see the header comment).
 PCAL_HD uint32_t hl_pair(uint32_t a, uint32_t b) {
-    return (a & (a >> 1) & 0x55555555u) | (b & (b << 1) & 0xAAAAAAAAu);
+    const uint32_t x = lop3<0x80>(a, a >> 1, 0x55555555u);  // a & (a>>1) & mask
+    const uint32_t y = b & (b + b);                          // hl of b at odd bits
+    return lop3<0xF8>(x, y, 0xAAAAAAAAu);                   // x | (y & mask)
+}
+
+// Thirty-two words of one column: the w stream (l and h bits) through two
+// Harley-Seal trees and one full adder at weight 16, the (h AND l) stream
+// through one tree on the 16 packed words.  Returns nothing; the carries of
+// weight 32 (w) and 16 (d) ripple into the upper planes.
+template <int U>
+PCAL_HD void add32(const uint32_t* x, uint32_t& w1, uint32_t& w2, uint32_t& w4, uint32_t& w8, uint32_t& w16,
+                   uint32_t (&wu)[U], uint32_t& d1, uint32_t& d2, uint32_t& d4, uint32_t& d8, uint32_t (&du)[U]) {
+    uint32_t d[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) d[m] = hl_pair(x[2 * m], x[2 * m + 1]);
+    const uint32_t a = harley_seal16(x, w1, w2, w4, w8);
+    const uint32_t b = harley_seal16(x + 16, w1, w2, w4, w8);
+    uint32_t c32;
+    csa(c32, w16, w16, a, b);
+    ripple<U>(wu, c32);
+    ripple<U>(du, harley_seal16(d, d1, d2, d4, d8));
 }
 
 // In-place transpose of two 16x16 bit matrices held in the low and high

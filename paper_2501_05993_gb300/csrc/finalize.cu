@@ -34,6 +34,7 @@ constexpr int kDftTonesPerCta = 32;
 struct FinArgs {
     int fmt;
     int bc;          // residues b per fold CTA
+    int tpb;         // threads per residue (power of two)
     int64_t L, N, so;
     int64_t q, rem, a0;  // samples in bin k: q + ((k - a0) mod L < rem)
     double lev0, c_l, c_h, c_hl;
@@ -80,28 +81,56 @@ __device__ __forceinline__ double take_bin(const FinArgs& a, int64_t k) {
     return v;
 }
 
-// FP64 block reduction in a fixed order (deterministic), any block size.
-__device__ double block_sum(double v, double* sm) {
-    const int t = threadIdx.x, n = blockDim.x;
-    sm[t] = v;
+// Warp sum with a fixed butterfly: every lane gets the same, deterministic
+// value.  Needs all 32 lanes.
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// K block-wide FP64 sums at once (fixed order: warp butterflies, then the
+// warp totals in warp order).  blockDim.x must be a multiple of 32; sm needs
+// 32*K doubles.  Every thread receives the sums.
+template <int K>
+__device__ void block_sums(double (&v)[K], double* sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int j = 0; j < K; ++j) v[j] = warp_sum(v[j]);
+    if (lane == 0)
+#pragma unroll
+        for (int j = 0; j < K; ++j) sm[warp * K + j] = v[j];
     __syncthreads();
-    int w = 1;
-    while (2 * w < n) w *= 2;
-    for (; w > 0; w >>= 1) {
-        if (t < w && t + w < n) sm[t] += sm[t + w];
-        __syncthreads();
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += sm[w * K + j];
+        v[j] = s;
     }
-    double r = sm[0];
     __syncthreads();
-    return r;
+}
+
+// Exclusive block-wide prefix sum (fixed order), any multiple of 32 threads.
+__device__ double block_exclusive_scan(double v, double* sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += u;
+    }
+    if (lane == 31) sm[warp] = inc;
+    __syncthreads();
+    double before = 0.0;
+    for (int w = 0; w < warp; ++w) before += sm[w];
+    __syncthreads();
+    return before + inc - v;
 }
 
 __device__ __forceinline__ double wrap_pi(double x) {
     // into [-pi, pi)
-    const double two_pi = 6.283185307179586476925;
-    double y = fmod(x + 3.141592653589793238463, two_pi);
-    if (y < 0) y += two_pi;
-    return y - 3.141592653589793238463;
+    const double two_pi = 6.283185307179586476925, inv = 0.159154943091895335769;
+    return x - two_pi * floor((x + 3.141592653589793238463) * inv);
 }
 
 // Tones [i0, i1) of the N-point DFT of P, in FP32; P is staged in shared
@@ -168,53 +197,44 @@ __device__ void tone_products(const FinArgs& a, double* sm) {
     double local = 0.0;
     for (int64_t i = c0; i < c1; ++i)
         if (i > 0) local += wrap_pi(ph[i] - ph[i - 1]);
-    sm[t] = local;
-    __syncthreads();
-    for (int w = 1; w < nt; w <<= 1) {  // inclusive Hillis-Steele scan
-        double v = t >= w ? sm[t - w] : 0.0;
-        __syncthreads();
-        sm[t] += v;
-        __syncthreads();
-    }
-    double run = ph[0] + (t > 0 ? sm[t - 1] : 0.0);
-    __syncthreads();
+    double run = ph[0] + block_exclusive_scan(local, sm);
     for (int64_t i = c0; i < c1; ++i) {
         if (i > 0) run += wrap_pi(ph[i] - ph[i - 1]);
         un[i] = run;
     }
     __syncthreads();
     // 3. weighted least squares of un[i] against f_i with w_i = |T_i|^2
-    double sw = 0, swf = 0, swu = 0;
+    double s3[3] = {0.0, 0.0, 0.0};
     for (int64_t i = c0; i < c1; ++i) {
-        double w = a.res[2 * i] * a.res[2 * i] + a.res[2 * i + 1] * a.res[2 * i + 1];
-        double f = (double)i * a.fc + a.fo;
-        sw += w;
-        swf += w * f;
-        swu += w * un[i];
+        const double w = a.res[2 * i] * a.res[2 * i] + a.res[2 * i + 1] * a.res[2 * i + 1];
+        s3[0] += w;
+        s3[1] += w * ((double)i * a.fc + a.fo);
+        s3[2] += w * un[i];
     }
-    const double W = block_sum(sw, sm), WF = block_sum(swf, sm), WU = block_sum(swu, sm);
+    block_sums<3>(s3, sm);
+    const double W = s3[0];
     double td = nan(""), sig = nan("");
     if (N >= 2 && W > 0) {
-        const double fbar = WF / W, ubar = WU / W;
-        double sff = 0, sfu = 0;
+        const double fbar = s3[1] / W, ubar = s3[2] / W;
+        double s2[2] = {0.0, 0.0};
         for (int64_t i = c0; i < c1; ++i) {
-            double w = a.res[2 * i] * a.res[2 * i] + a.res[2 * i + 1] * a.res[2 * i + 1];
-            double df = (double)i * a.fc + a.fo - fbar;
-            sff += w * df * df;
-            sfu += w * df * (un[i] - ubar);
+            const double w = a.res[2 * i] * a.res[2 * i] + a.res[2 * i + 1] * a.res[2 * i + 1];
+            const double df = (double)i * a.fc + a.fo - fbar;
+            s2[0] += w * df * df;
+            s2[1] += w * df * (un[i] - ubar);
         }
-        const double SFF = block_sum(sff, sm), SFU = block_sum(sfu, sm);
-        if (SFF > 0) {
-            const double slope = SFU / SFF;
-            double sr = 0;
+        block_sums<2>(s2, sm);
+        if (s2[0] > 0) {
+            const double slope = s2[1] / s2[0];
+            double s1[1] = {0.0};
             for (int64_t i = c0; i < c1; ++i) {
-                double w = a.res[2 * i] * a.res[2 * i] + a.res[2 * i + 1] * a.res[2 * i + 1];
-                double r = un[i] - ubar - slope * ((double)i * a.fc + a.fo - fbar);
-                sr += w * r * r;
+                const double w = a.res[2 * i] * a.res[2 * i] + a.res[2 * i + 1] * a.res[2 * i + 1];
+                const double r = un[i] - ubar - slope * ((double)i * a.fc + a.fo - fbar);
+                s1[0] += w * r * r;
             }
-            const double SR = block_sum(sr, sm);
+            block_sums<1>(s1, sm);
             td = slope / 6.283185307179586476925;
-            if (N > 2) sig = sqrt((SR / (double)(N - 2)) / SFF) / 6.283185307179586476925;
+            if (N > 2) sig = sqrt((s1[0] / (double)(N - 2)) / s2[0]) / 6.283185307179586476925;
         }
     }
     if (t == 0) {
@@ -225,16 +245,20 @@ __device__ void tone_products(const FinArgs& a, double* sm) {
 }
 
 // Decode + FP64 rotation + fold of whole residues; the last CTA continues.
+// Thread t works on residue b = blockIdx.x*bc + t/tpb and bins b + m*N for
+// m = t%tpb, t%tpb + tpb, ...; the tpb threads of a residue are contiguous
+// (tpb a power of two) and combine with shuffles, then across warps.
 __global__ void fin_fold_kernel(FinArgs a) {
     extern __shared__ double2 smem2[];
     __shared__ bool is_last;
-    const int bc = a.bc;
-    const int mstep = blockDim.x / bc;
-    const int64_t b = (int64_t)blockIdx.x * bc + threadIdx.x % bc;
+    const int tpb = a.tpb;
+    const int bl = threadIdx.x / tpb, sub = threadIdx.x % tpb;
+    const int64_t b = (int64_t)blockIdx.x * a.bc + bl;
+    const bool active = bl < a.bc && b < a.N;
     const int64_t per = a.L / a.N;
     double re = 0.0, im = 0.0;
-    if ((int)threadIdx.x < mstep * bc && b < a.N) {
-        for (int64_t m = threadIdx.x / bc; m < per; m += mstep) {
+    if (active) {
+        for (int64_t m = sub; m < per; m += tpb) {
             const int64_t k = b + m * a.N;
             const double S = take_bin(a, k);
             const double2 w = a.tw[(a.so * k) % a.L];
@@ -242,16 +266,26 @@ __global__ void fin_fold_kernel(FinArgs a) {
             im = fma(S, w.y, im);
         }
     }
-    smem2[threadIdx.x] = make_double2(re, im);
-    __syncthreads();
-    if ((int)threadIdx.x < bc && b < a.N) {
-        double sr = 0.0, si = 0.0;
-        for (int j = 0; j < mstep; ++j) {
-            const double2 v = smem2[threadIdx.x + j * bc];
-            sr += v.x;
-            si += v.y;
+    const int width = tpb < 32 ? tpb : 32;
+    for (int o = width / 2; o > 0; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (tpb <= 32) {
+        if (active && sub == 0) a.P[b] = make_double2(re, im);
+    } else {
+        double2* wsum = smem2;
+        if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = make_double2(re, im);
+        __syncthreads();
+        if (active && sub == 0) {
+            double sr = 0.0, si = 0.0;
+            const int w0 = threadIdx.x >> 5;
+            for (int w = 0; w < tpb / 32; ++w) {
+                sr += wsum[w0 + w].x;
+                si += wsum[w0 + w].y;
+            }
+            a.P[b] = make_double2(sr, si);
         }
-        a.P[b] = make_double2(sr, si);
     }
     __threadfence();
     __syncthreads();
@@ -338,21 +372,32 @@ cudaError_t launch_finalize(pcal_plan* p, cudaStream_t s) {
     int G = (int)(g.N < p->num_sms ? g.N : p->num_sms);
     a.bc = (int)((g.N + G - 1) / G);
     G = (int)((g.N + a.bc - 1) / a.bc);
-    // A multiple of 32 (the DFT's shuffles need whole warps); threads past
-    // (threads / bc) * bc stay idle in the fold.
-    int threads = a.bc <= 256 ? 256 : (int)((a.bc + 31) / 32 * 32);
+    // tpb = the largest power of two with bc*tpb <= 256; the block is a
+    // multiple of 32 threads (the shuffles and the DFT need whole warps)
+    a.tpb = 1;
+    while (a.bc * a.tpb * 2 <= 256) a.tpb *= 2;
+    int threads = (a.bc * a.tpb + 31) / 32 * 32;
     size_t smem = (size_t)threads * sizeof(double2);
     if (g.N <= kDftInFoldMaxN) smem += (size_t)g.N * sizeof(float2);
-    cudaError_t e = cudaFuncSetAttribute(fin_fold_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
+    static size_t fold_smem_set = 0;
+    if (smem > fold_smem_set) {
+        e = cudaFuncSetAttribute(fin_fold_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        fold_smem_set = smem;
+    }
     fin_fold_kernel<<<G, threads, smem, s>>>(a);
     p->stats.kernel_launches += 1;
     e = cudaGetLastError();
     if (e != cudaSuccess || g.N <= kDftInFoldMaxN) return e;
     const int threads2 = 256;
     const size_t smem2 = threads2 * sizeof(double2) + (size_t)g.N * sizeof(float2);
-    e = cudaFuncSetAttribute(fin_dft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
-    if (e != cudaSuccess) return e;
+    static size_t dft_smem_set = 0;
+    if (smem2 > dft_smem_set) {
+        e = cudaFuncSetAttribute(fin_dft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+        if (e != cudaSuccess) return e;
+        dft_smem_set = smem2;
+    }
     fin_dft_kernel<<<(unsigned)((g.N + kDftTonesPerCta - 1) / kDftTonesPerCta), threads2, smem2, s>>>(a);
     p->stats.kernel_launches += 1;
     return cudaGetLastError();

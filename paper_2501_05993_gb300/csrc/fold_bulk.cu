@@ -35,15 +35,16 @@
 
 namespace {
 
-constexpr int kMaxBlock = 512;           // consumer threads + producer warp
-constexpr int kSmemBudget = 200 * 1024;  // dynamic shared memory per CTA
-constexpr uint32_t kSpinLimit = 1u << 22;
+constexpr int kMaxBlock = 896;           // consumer warps + producer warp
+constexpr int kSmemBudget = 220 * 1024;  // dynamic shared memory per CTA
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // give up a wait after 2 s
 
 struct BulkArgs {
     int cols_total;   // words per row
     int col_width;    // C_w
     int col_groups;   // G_c
-    int replicas;     // r
+    int replicas;     // r consumer groups
+    int wpr;          // warps per group = ceil(col_width / 32)
     int box_rows;     // rows per stage
     int stages;
     int consumers;    // C_w * r
@@ -81,11 +82,12 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                  : "memory");
 }
 
-__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+// try_wait suspends the thread in hardware for a while instead of spinning.
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
         : "r"(smem_addr(bar)), "r"(parity)
@@ -93,13 +95,19 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait for the phase of `parity` to complete.
-__device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (uint32_t i = 0; i < kSpinLimit; ++i) {
-        if (mbar_test(bar, parity)) return true;
-        if (i > 64) __nanosleep(i < 4096 ? 32 : 256);
-    }
-    return false;
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase of `parity` to complete; false after kWaitLimitNs.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try(bar, parity))
+        if (global_ns() - t0 > kWaitLimitNs) return false;
+    return true;
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
@@ -115,21 +123,17 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
 
 template <int U>
 struct Acc2 {
-    // w stream: 4 Harley-Seal planes + U upper planes; d stream: 3 + U.
-    uint32_t w1 = 0, w2 = 0, w4 = 0, w8 = 0, wu[U];
-    uint32_t d1 = 0, d2 = 0, d4 = 0, du[U];
+    // w stream: planes of weight 1..16 + U upper planes (weight 32 on);
+    // d stream: planes of weight 1..8 + U upper planes (weight 16 on).
+    uint32_t w1 = 0, w2 = 0, w4 = 0, w8 = 0, w16 = 0, wu[U];
+    uint32_t d1 = 0, d2 = 0, d4 = 0, d8 = 0, du[U];
     __device__ Acc2() {
 #pragma unroll
         for (int u = 0; u < U; ++u) wu[u] = du[u] = 0;
     }
-    // 16 words of this thread's column, from 16 of its rows.
-    __device__ __forceinline__ void add16(const uint32_t (&x)[16]) {
-        using namespace pcal_bits;
-        uint32_t d[8];
-#pragma unroll
-        for (int m = 0; m < 8; ++m) d[m] = hl_pair(x[2 * m], x[2 * m + 1]);
-        ripple<U>(wu, harley_seal16(x, w1, w2, w4, w8));
-        ripple<U>(du, harley_seal8(d, d1, d2, d4));
+    // 32 words of this thread's column, from 32 of its rows.
+    __device__ __forceinline__ void add32(const uint32_t (&x)[32]) {
+        pcal_bits::add32<U>(x, w1, w2, w4, w8, w16, wu, d1, d2, d4, d8, du);
     }
 };
 
@@ -155,12 +159,18 @@ struct AccF {
 
 // ---- the kernel ------------------------------------------------------------------
 // FMT: PCAL_2BIT, PCAL_I8 or PCAL_F32.  U: upper bit planes (2-bit only).
+//
+// Threads: `replicas` groups of `wpr` consumer warps, then one producer warp.
+// Lane c < col_width of a group owns column c0 + c; group q consumes the
+// boxes q, q + r, q + 2r, ... whole, so a box is read by one group only and
+// each group's warps release its stage with one arrival per warp.
 template <int FMT, int U>
 __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                  const BulkArgs a) {
     extern __shared__ __align__(1024) uint8_t smem[];
     const int tid = threadIdx.x;
-    const int n_cons_warps = (a.consumers + 31) / 32;
+    const int group_threads = a.wpr * 32;
+    const int n_cons_warps = a.wpr * a.replicas;
     const int producer_warp = n_cons_warps;
     const int cg = blockIdx.x % a.col_groups;
     const int64_t rg = blockIdx.x / a.col_groups;
@@ -179,19 +189,19 @@ __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_co
         s_failed = 0;
         for (int s = 0; s < a.stages; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], n_cons_warps);
+            mbar_init(&empty[s], a.wpr);
         }
         fence_barrier_init();
     }
-    // zero the merge area
     {
         const int words = FMT == PCAL_2BIT ? a.col_width * 32 : (FMT == PCAL_I8 ? a.col_width * 4 : 0);
         for (int i = tid; i < words; i += blockDim.x) reinterpret_cast<uint32_t*>(merge)[i] = 0;
     }
     __syncthreads();
 
-    const int col = tid % a.col_width;
-    const int q = tid / a.col_width;
+    const int q = tid / group_threads;   // replica group
+    const int col = tid % group_threads; // column within the tile
+    const bool active = tid < n_cons_warps * 32 && col < a.col_width;
     Acc2<(FMT == PCAL_2BIT ? U : 1)> acc2;
     Acc8 acc8;
     AccF accf;
@@ -225,11 +235,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_co
         }
     } else {
         // ---------------- consumers ----------------
-        // Every lane of a consumer warp takes part in the waits and in the
-        // per-warp release; lanes past `consumers` only skip the arithmetic.
-        const bool active = tid < a.consumers;
-        const int rows_per_rep = a.box_rows / a.replicas;
-        for (int j = 0; j < n_boxes; ++j) {
+        for (int j = q; j < n_boxes; j += a.replicas) {
             const int s = j % a.stages;
             const uint32_t use = j / a.stages;
             if (!mbar_wait(&full[s], use & 1)) {
@@ -237,21 +243,22 @@ __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_co
                 s_failed = 1;
                 break;
             }
-            const uint32_t* tile = reinterpret_cast<const uint32_t*>(smem + (size_t)s * a.stage_stride);
+            const uint32_t* p = reinterpret_cast<const uint32_t*>(smem + (size_t)s * a.stage_stride) + col;
             if (active) {
                 if (FMT == PCAL_2BIT) {
-                    for (int b = 0; b < rows_per_rep; b += 16) {
-                        uint32_t x[16];
+                    for (int b = 0; b < a.box_rows; b += 32) {
+                        uint32_t x[32];
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) x[i] = tile[(q + a.replicas * (b + i)) * a.col_width + col];
-                        acc2.add16(x);
+                        for (int i = 0; i < 32; ++i) x[i] = p[i * a.col_width];
+                        acc2.add32(x);
+                        p += 32 * a.col_width;
                     }
                 } else if (FMT == PCAL_I8) {
-#pragma unroll 4
-                    for (int i = 0; i < rows_per_rep; ++i) acc8.add(tile[(q + a.replicas * i) * a.col_width + col]);
+#pragma unroll 8
+                    for (int i = 0; i < a.box_rows; ++i) acc8.add(p[i * a.col_width]);
                 } else {
-#pragma unroll 4
-                    for (int i = 0; i < rows_per_rep; ++i) accf.add(tile[(q + a.replicas * i) * a.col_width + col]);
+#pragma unroll 8
+                    for (int i = 0; i < a.box_rows; ++i) accf.add(p[i * a.col_width]);
                 }
             }
             __syncwarp();
@@ -262,39 +269,62 @@ __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_co
     if (s_failed) return;
 
     // ---------------- merge replicas, then flush ----------------
-    const int gcol = c0 + col;
+    // The stage buffers are free now (every fill landed and was consumed).
     if (FMT == PCAL_2BIT) {
-        if (tid < a.consumers) {
-            uint32_t W[16], D[16];
+        uint32_t W[16], D[16];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) W[i] = D[i] = 0;
-            W[0] = acc2.w1;
-            W[1] = acc2.w2;
-            W[2] = acc2.w4;
-            W[3] = acc2.w8;
-            D[0] = acc2.d1;
-            D[1] = acc2.d2;
-            D[2] = acc2.d4;
+        for (int i = 0; i < 16; ++i) W[i] = D[i] = 0;
+        W[0] = acc2.w1;
+        W[1] = acc2.w2;
+        W[2] = acc2.w4;
+        W[3] = acc2.w8;
+        W[4] = acc2.w16;
+        D[0] = acc2.d1;
+        D[1] = acc2.d2;
+        D[2] = acc2.d4;
+        D[3] = acc2.d8;
 #pragma unroll
-            for (int u = 0; u < (FMT == PCAL_2BIT ? U : 1); ++u) {
-                if (4 + u < 16) W[4 + u] = acc2.wu[u];
-                if (3 + u < 16) D[3 + u] = acc2.du[u];
+        for (int u = 0; u < (FMT == PCAL_2BIT ? U : 1); ++u) {
+            if (5 + u < 16) W[5 + u] = acc2.wu[u];
+            if (4 + u < 16) D[4 + u] = acc2.du[u];
+        }
+        // replicas add up pairwise in the bit-plane domain (ripple-carry adds
+        // of 16-plane numbers; per-CTA counts stay below 2^16)
+        uint32_t* scratch = reinterpret_cast<uint32_t*>(smem);
+        for (int step = 1; step < a.replicas; step <<= 1) {
+            if (active && q % (2 * step) == step) {
+                uint32_t* dst = scratch + ((size_t)q * a.col_width + col) * 32;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    dst[i] = W[i];
+                    dst[16 + i] = D[i];
+                }
             }
+            __syncthreads();
+            if (active && q % (2 * step) == 0 && q + step < a.replicas) {
+                const uint32_t* src = scratch + ((size_t)(q + step) * a.col_width + col) * 32;
+                uint32_t cw = 0, cd = 0;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const uint32_t bw = src[i], bd = src[16 + i];
+                    const uint32_t sw = pcal_bits::lop3<pcal_bits::kXor3>(W[i], bw, cw);
+                    cw = pcal_bits::lop3<pcal_bits::kMaj3>(W[i], bw, cw);
+                    W[i] = sw;
+                    const uint32_t sd = pcal_bits::lop3<pcal_bits::kXor3>(D[i], bd, cd);
+                    cd = pcal_bits::lop3<pcal_bits::kMaj3>(D[i], bd, cd);
+                    D[i] = sd;
+                }
+            }
+            __syncthreads();
+        }
+        if (active && q == 0) {
             pcal_bits::transpose16x2(W);
             pcal_bits::transpose16x2(D);
             uint32_t* m = reinterpret_cast<uint32_t*>(merge) + col * 32;
-            if (a.replicas == 1) {
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    m[i] = W[i];
-                    m[16 + i] = D[i];
-                }
-            } else {
-#pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    atomicAdd(&m[i], W[i]);
-                    atomicAdd(&m[16 + i], D[i]);
-                }
+            for (int i = 0; i < 16; ++i) {
+                m[i] = W[i];
+                m[16 + i] = D[i];
             }
         }
         __syncthreads();
@@ -316,7 +346,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_co
         }
     } else if (FMT == PCAL_I8) {
         int* m = reinterpret_cast<int*>(merge);
-        if (tid < a.consumers) {
+        if (active) {
 #pragma unroll
             for (int j = 0; j < 4; ++j)
                 if (acc8.s[j]) atomicAdd(&m[col * 4 + j], acc8.s[j]);
@@ -332,9 +362,9 @@ __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_co
         // f32: replicas in a fixed order, then one partial per column per
         // row group; a second kernel sums the partials per bin.
         float2* m = reinterpret_cast<float2*>(merge);
-        if (tid < a.consumers) m[q * a.col_width + col] = make_float2(accf.s, accf.c);
+        if (active) m[q * a.col_width + col] = make_float2(accf.s, accf.c);
         __syncthreads();
-        if (tid < a.col_width && gcol < a.cols_total) {
+        if (tid < a.col_width && c0 + tid < a.cols_total) {
             float s = 0.f, c = 0.f;
             for (int r = 0; r < a.replicas; ++r) {
                 const float2 v = m[r * a.col_width + tid];
@@ -342,7 +372,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_co
                 c += (fabsf(s) >= fabsf(v.x) ? (s - t) + v.x : (v.x - t) + s) + v.y;
                 s = t;
             }
-            a.partf[rg * a.cols_total + gcol] = make_float2(s, c);
+            a.partf[rg * a.cols_total + c0 + tid] = make_float2(s, c);
         }
     }
 }
@@ -386,8 +416,12 @@ int bits_for(int64_t v) {
 template <int FMT, int U>
 cudaError_t launch_one(const CUtensorMap& map, const BulkArgs& a, int grid, int block, size_t smem, cudaStream_t s) {
     auto k = bulk_fold_kernel<FMT, U>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    static size_t smem_set = 0;  // per instantiation; the attribute only grows
+    if (smem > smem_set) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        smem_set = smem;
+    }
     k<<<grid, block, smem, s>>>(map, a);
     return cudaGetLastError();
 }
@@ -399,6 +433,7 @@ int bulk_tiling(const pcal_plan* p, int64_t n_rows, BulkTiling* t) {
     const int cols = (int)(p->g.row_samples / spw);
     BulkTiling z{};
     z.cols_total = cols;
+    // column groups of at most 256 words (the TMA box limit), 32-byte wide
     int gc = (cols + 255) / 256;
     int cw = (cols + gc - 1) / gc;
     cw = (cw + 7) / 8 * 8;
@@ -406,25 +441,27 @@ int bulk_tiling(const pcal_plan* p, int64_t n_rows, BulkTiling* t) {
     gc = (cols + cw - 1) / cw;
     z.col_width = cw;
     z.col_groups = gc;
-    int r = (kMaxBlock - 32) / cw;
+    const int wpr = (cw + 31) / 32;
+    int r = (kMaxBlock / 32 - 1) / wpr;
     if (r > 8) r = 8;
     if (r < 1) r = 1;
     z.replicas = r;
-    // a stage of about 24 KB, rows a multiple of 16*r (2-bit blocks of 16)
-    const int unit = (p->g.format == PCAL_2BIT ? 16 : 1) * r;
-    int units = (24 * 1024) / (unit * cw * 4);
+    // a stage of about 24-32 KB; 2-bit boxes are whole 32-row blocks
+    const int unit = p->g.format == PCAL_2BIT ? 32 : 8;
+    int units = (28 * 1024) / (unit * cw * 4);
     if (units < 1) units = 1;
     int box = unit * units;
     while (box > 256) box -= unit;
-    if (box < unit) return -1;
     z.box_rows = box;
     const size_t stage = (size_t)box * cw * 4;
     const size_t stage_al = (stage + 1023) / 1024 * 1024;
-    size_t merge = p->g.format == PCAL_2BIT ? (size_t)cw * 128 : (p->g.format == PCAL_I8 ? (size_t)cw * 16
-                                                                                          : (size_t)cw * r * 8);
+    const size_t merge = p->g.format == PCAL_2BIT ? (size_t)cw * 128
+                         : (p->g.format == PCAL_I8 ? (size_t)cw * 16 : (size_t)cw * r * 8);
     int stages = (int)((kSmemBudget - merge - 1024) / stage_al);
     if (stages > 8) stages = 8;
-    if (stages < 2) return -1;
+    if (stages < 3) return -1;
+    // the 2-bit replica merge reuses the stage buffers as scratch
+    if (p->g.format == PCAL_2BIT && (size_t)r * cw * 128 > (size_t)stages * stage_al) return -1;
     z.stages = stages;
     // row groups: one wave over the SMs, rows per CTA a multiple of the box
     // and small enough for 16-bit per-CTA counts
@@ -439,10 +476,11 @@ int bulk_tiling(const pcal_plan* p, int64_t n_rows, BulkTiling* t) {
     z.rows_per_cta = per;
     z.upper_planes = 0;
     if (p->g.format == PCAL_2BIT) {
-        const int64_t blocks = per / r / 16;
-        z.upper_planes = bits_for(blocks);
+        const int64_t boxes = per / box;
+        const int64_t rows_per_thread = (boxes + r - 1) / r * box;
+        z.upper_planes = bits_for(rows_per_thread / 32);
     }
-    z.threads = ((cw * r + 31) / 32 + 1) * 32;
+    z.threads = (wpr * r + 1) * 32;
     z.smem_bytes = (size_t)stages * stage_al + 16 * (size_t)stages + merge;
     *t = z;
     return 0;
@@ -450,28 +488,41 @@ int bulk_tiling(const pcal_plan* p, int64_t n_rows, BulkTiling* t) {
 
 cudaError_t launch_bulk(pcal_plan* p, const void* d_rows, int64_t n_rows, int64_t k_a, cudaStream_t s, int* launched) {
     *launched = 0;
-    BulkTiling t;
-    if (bulk_tiling(p, n_rows, &t) != 0) return cudaErrorInvalidConfiguration;
-    PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
-    if (!enc) return cudaErrorNotSupported;
-    const int spw = p->g.samples_per_byte_x4;
-    CUtensorMap map;
-    cuuint64_t dims[2] = {(cuuint64_t)t.cols_total, (cuuint64_t)n_rows};
-    cuuint64_t strides[1] = {(cuuint64_t)(p->g.row_samples / spw * 4)};
-    cuuint32_t box[2] = {(cuuint32_t)t.col_width, (cuuint32_t)t.box_rows};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<void*>(d_rows), dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    const BulkMapEntry* hit = nullptr;
+    for (int i = 0; i < kBulkMapCache; ++i)
+        if (p->map_cache[i].ptr == d_rows && p->map_cache[i].rows == n_rows) hit = &p->map_cache[i];
+    if (!hit) {
+        BulkMapEntry ent{};
+        if (bulk_tiling(p, n_rows, &ent.tiling) != 0) return cudaErrorInvalidConfiguration;
+        const BulkTiling& t = ent.tiling;
+        PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
+        if (!enc) return cudaErrorNotSupported;
+        const int spw = p->g.samples_per_byte_x4;
+        cuuint64_t dims[2] = {(cuuint64_t)t.cols_total, (cuuint64_t)n_rows};
+        cuuint64_t strides[1] = {(cuuint64_t)(p->g.row_samples / spw * 4)};
+        cuuint32_t box[2] = {(cuuint32_t)t.col_width, (cuuint32_t)t.box_rows};
+        cuuint32_t estr[2] = {1, 1};
+        CUresult r = enc(&ent.map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<void*>(d_rows), dims, strides, box,
+                         estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+        ent.ptr = d_rows;
+        ent.rows = n_rows;
+        p->map_cache[p->map_next] = ent;
+        hit = &p->map_cache[p->map_next];
+        p->map_next = (p->map_next + 1) % kBulkMapCache;
+    }
+    const BulkTiling& t = hit->tiling;
+    const CUtensorMap& map = hit->map;
     BulkArgs a{};
     a.cols_total = t.cols_total;
     a.col_width = t.col_width;
     a.col_groups = t.col_groups;
     a.replicas = t.replicas;
+    a.wpr = (t.col_width + 31) / 32;
     a.box_rows = t.box_rows;
     a.stages = t.stages;
-    a.consumers = t.col_width * t.replicas;
+    a.consumers = a.wpr * 32 * t.replicas;
     a.tx_bytes = (uint32_t)((size_t)t.box_rows * t.col_width * 4);
     a.stage_stride = (a.tx_bytes + 1023u) / 1024u * 1024u;
     a.rows_per_cta = t.rows_per_cta;
@@ -506,18 +557,16 @@ cudaError_t launch_bulk(pcal_plan* p, const void* d_rows, int64_t n_rows, int64_
         e = launch_one<PCAL_I8, 1>(map, a, grid, t.threads, t.smem_bytes, s);
     } else {
         const int u = t.upper_planes;
-        if (u <= 2)
-            e = launch_one<PCAL_2BIT, 2>(map, a, grid, t.threads, t.smem_bytes, s);
-        else if (u <= 4)
-            e = launch_one<PCAL_2BIT, 4>(map, a, grid, t.threads, t.smem_bytes, s);
-        else if (u <= 6)
-            e = launch_one<PCAL_2BIT, 6>(map, a, grid, t.threads, t.smem_bytes, s);
-        else if (u <= 8)
-            e = launch_one<PCAL_2BIT, 8>(map, a, grid, t.threads, t.smem_bytes, s);
-        else if (u <= 10)
-            e = launch_one<PCAL_2BIT, 10>(map, a, grid, t.threads, t.smem_bytes, s);
+        if (u <= 3)
+            e = launch_one<PCAL_2BIT, 3>(map, a, grid, t.threads, t.smem_bytes, s);
+        else if (u <= 5)
+            e = launch_one<PCAL_2BIT, 5>(map, a, grid, t.threads, t.smem_bytes, s);
+        else if (u <= 7)
+            e = launch_one<PCAL_2BIT, 7>(map, a, grid, t.threads, t.smem_bytes, s);
+        else if (u <= 9)
+            e = launch_one<PCAL_2BIT, 9>(map, a, grid, t.threads, t.smem_bytes, s);
         else
-            e = launch_one<PCAL_2BIT, 12>(map, a, grid, t.threads, t.smem_bytes, s);
+            e = launch_one<PCAL_2BIT, 11>(map, a, grid, t.threads, t.smem_bytes, s);
     }
     if (e == cudaSuccess) {
         *launched = 1;

@@ -20,6 +20,31 @@
 #define PCAL_DERR_EMPTY_WAIT 2u  // the producer gave up waiting for a slot
 #define PCAL_DERR_DRAIN_WAIT 4u  // a CTA gave up draining its copies
 
+// Tile plan of the bulk kernel for a given plan and row count (host only).
+struct BulkTiling {
+    int cols_total;    // words per row
+    int col_width;     // words per column group (tile width)
+    int col_groups;    // G_c
+    int replicas;      // consumer threads per column
+    int box_rows;      // rows per TMA box (stage)
+    int stages;        // pipeline depth
+    int64_t row_groups;      // G_r
+    int64_t rows_per_cta;    // multiple of box_rows
+    int upper_planes;  // 2-bit: bit planes above the Harley-Seal tree
+    int threads;       // consumer threads + 1 producer warp
+    size_t smem_bytes;
+};
+
+// Encoded tensor maps of recent bulk inputs, so that repeated calls on the
+// same buffers skip the host-side encode.
+struct BulkMapEntry {
+    const void* ptr;
+    int64_t rows;
+    BulkTiling tiling;
+    CUtensorMap map;
+};
+constexpr int kBulkMapCache = 16;
+
 struct pcal_plan {
     pcal_geometry g;
     double levels[4];
@@ -54,6 +79,8 @@ struct pcal_plan {
     cudaStream_t copy_stream;     // H2D copies of pcal_accumulate_host
     bool results_valid;
     pcal_stats stats;
+    BulkMapEntry map_cache[kBulkMapCache];
+    int map_next;
 };
 
 // ---- launchers (return a cudaError_t of the launch) -------------------------
@@ -70,19 +97,4 @@ cudaError_t launch_finalize(pcal_plan* p, cudaStream_t s);
 cudaError_t launch_bulk(pcal_plan* p, const void* d_rows, int64_t n_rows, int64_t k_a, cudaStream_t s,
                         int* launched);
 
-// Tile plan of the bulk kernel for a given plan and row count (host only),
-// exposed so that tests can check the work split.
-struct BulkTiling {
-    int cols_total;    // words per row
-    int col_width;     // words per column group (tile width)
-    int col_groups;    // G_c
-    int replicas;      // consumer threads per column
-    int box_rows;      // rows per TMA box (stage)
-    int stages;        // pipeline depth
-    int64_t row_groups;      // G_r
-    int64_t rows_per_cta;    // multiple of box_rows
-    int upper_planes;  // 2-bit: bit planes above the Harley-Seal tree
-    int threads;       // consumer threads + 1 producer warp
-    size_t smem_bytes;
-};
 int bulk_tiling(const pcal_plan* p, int64_t n_rows, BulkTiling* t);

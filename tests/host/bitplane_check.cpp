@@ -7,15 +7,17 @@
 
 #include "bitplane.cuh"
 
+static uint32_t d3_unused() { return 0; }
+
 template <int U>
 int run(uint64_t seed, int blocks, bool all_ones) {
     std::mt19937_64 rng(seed);
-    uint32_t w1 = 0, w2 = 0, w4 = 0, w8 = 0, wu[U] = {0};
-    uint32_t d1 = 0, d2 = 0, d4 = 0, du[U] = {0};
+    uint32_t w1 = 0, w2 = 0, w4 = 0, w8 = 0, w16 = 0, wu[U] = {0};
+    uint32_t d1 = 0, d2 = 0, d4 = 0, d8 = 0, du[U] = {0};
     uint64_t ref_l[16] = {0}, ref_h[16] = {0}, ref_hl[16] = {0};
     for (int b = 0; b < blocks; ++b) {
-        uint32_t x[16], d[8];
-        for (int i = 0; i < 16; ++i) {
+        uint32_t x[32];
+        for (int i = 0; i < 32; ++i) {
             x[i] = all_ones ? 0xFFFFFFFFu : (uint32_t)rng();
             for (int j = 0; j < 16; ++j) {
                 uint32_t c = (x[i] >> (2 * j)) & 3u;
@@ -24,17 +26,16 @@ int run(uint64_t seed, int blocks, bool all_ones) {
                 ref_hl[j] += (c == 3u);
             }
         }
-        for (int m = 0; m < 8; ++m) d[m] = pcal_bits::hl_pair(x[2 * m], x[2 * m + 1]);
-        pcal_bits::ripple<U>(wu, pcal_bits::harley_seal16(x, w1, w2, w4, w8));
-        pcal_bits::ripple<U>(du, pcal_bits::harley_seal8(d, d1, d2, d4));
+        pcal_bits::add32<U>(x, w1, w2, w4, w8, w16, wu, d1, d2, d4, d8, du);
     }
-    uint32_t W[16] = {w1, w2, w4, w8}, D[16] = {d1, d2, d4};
+    uint32_t W[16] = {w1, w2, w4, w8, w16}, D[16] = {d1, d2, d3_unused(), d8};
+    D[2] = d4;
     for (int u = 0; u < U; ++u) {
-        if (4 + u < 16) W[4 + u] = wu[u];
-        if (3 + u < 16) D[3 + u] = du[u];
+        if (5 + u < 16) W[5 + u] = wu[u];
+        if (4 + u < 16) D[4 + u] = du[u];
     }
-    for (int i = 4 + U; i < 16; ++i) W[i] = 0;
-    for (int i = 3 + U; i < 16; ++i) D[i] = 0;
+    for (int i = 5 + U; i < 16; ++i) W[i] = 0;
+    for (int i = 4 + U; i < 16; ++i) D[i] = 0;
     pcal_bits::transpose16x2(W);
     pcal_bits::transpose16x2(D);
     auto lane = [](const uint32_t* A, int p) { return (A[p & 15] >> (16 * (p >> 4))) & 0xFFFFu; };
@@ -55,16 +56,16 @@ int run(uint64_t seed, int blocks, bool all_ones) {
 int main() {
     int bad = 0;
     for (int s = 0; s < 20; ++s) {
-        bad += run<2>(s, 3, false);
-        bad += run<4>(100 + s, 15, false);
-        bad += run<6>(200 + s, 63, false);
-        bad += run<8>(300 + s, 255, false);
-        bad += run<10>(400 + s, 700, false);
+        bad += run<3>(s, 3, false);
+        bad += run<5>(100 + s, 31, false);
+        bad += run<7>(200 + s, 127, false);
+        bad += run<9>(300 + s, 300, false);
+        bad += run<11>(400 + s, 700, false);
     }
     // largest counts each template supports: every bit set in every word
-    bad += run<2>(1, 3, true);
-    bad += run<6>(1, 63, true);
-    bad += run<12>(1, 4095, true);
+    bad += run<3>(1, 7, true);
+    bad += run<5>(1, 31, true);
+    bad += run<11>(1, 2047, true);
     std::printf(bad ? "FAIL %d\n" : "OK\n", bad);
     return bad != 0;
 }
