@@ -199,6 +199,22 @@ typedef struct {
 
 int pcal_get_stats(const pcal_plan* plan, pcal_stats* out);
 
+/*
+ * Work split of the bulk fold kernel (host only, no CUDA call), for tests and
+ * diagnostics: how `n_rows` rows of `row_samples` samples are tiled over
+ * `num_sms` SMs for a plan with these parameters.  PCAL_EINVAL when no tile
+ * plan exists (such inputs are folded by the ragged kernel instead).
+ */
+typedef struct {
+    int32_t cols_total, col_width, col_groups, replicas, box_rows, stages;
+    int64_t row_groups, rows_per_cta;
+    int32_t upper_planes, threads;
+    int64_t smem_bytes;
+} pcal_tiling;
+
+int pcal_bulk_tiling(double fs, double f_comb, double f_offset, int N, int sample_format, int num_sms,
+                     int64_t n_rows, pcal_tiling* out);
+
 /* Static name of a status code. */
 const char* pcal_strerror(int code);
 

@@ -43,6 +43,16 @@ class Stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Tiling(ctypes.Structure):
+    _fields_ = [("cols_total", ctypes.c_int32), ("col_width", ctypes.c_int32), ("col_groups", ctypes.c_int32),
+                ("replicas", ctypes.c_int32), ("box_rows", ctypes.c_int32), ("stages", ctypes.c_int32),
+                ("row_groups", ctypes.c_int64), ("rows_per_cta", ctypes.c_int64), ("upper_planes", ctypes.c_int32),
+                ("threads", ctypes.c_int32), ("smem_bytes", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class PcalError(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = code
@@ -79,6 +89,7 @@ def load(path: str | None = None):
         "pcal_get_bins": ([vp, vp], ci),
         "pcal_get_stats": ([vp, P(Stats)], ci),
         "pcal_strerror": ([ci], ctypes.c_char_p),
+        "pcal_bulk_tiling": ([dbl, dbl, dbl, ci, ci, ci, i64, P(Tiling)], ci),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -189,6 +200,13 @@ def pcal_get_bins(plan: int, geometry: Geometry) -> np.ndarray:
         out = np.zeros(L, dtype=np.float64)
     _check(load().pcal_get_bins(plan, out.ctypes.data), "pcal_get_bins")
     return out
+
+
+def pcal_bulk_tiling(fs, f_comb, f_offset, N, sample_format, num_sms, n_rows) -> Tiling:
+    t = Tiling()
+    _check(load().pcal_bulk_tiling(float(fs), float(f_comb), float(f_offset), int(N), int(sample_format),
+                                   int(num_sms), int(n_rows), ctypes.byref(t)), "pcal_bulk_tiling")
+    return t
 
 
 def pcal_get_stats(plan: int) -> Stats:

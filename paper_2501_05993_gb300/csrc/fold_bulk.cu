@@ -27,6 +27,7 @@
 // exact); float32 tiles write fixed-order partials that a second kernel sums
 // per bin in a fixed order, so float results are deterministic.
 #include <stdio.h>
+#include <string.h>
 
 #include <cudaTypedefs.h>
 
@@ -442,10 +443,9 @@ int bulk_tiling(const pcal_plan* p, int64_t n_rows, BulkTiling* t) {
     z.col_width = cw;
     z.col_groups = gc;
     const int wpr = (cw + 31) / 32;
-    int r = (kMaxBlock / 32 - 1) / wpr;
-    if (r > 8) r = 8;
-    if (r < 1) r = 1;
-    z.replicas = r;
+    int r_max = (kMaxBlock / 32 - 1) / wpr;
+    if (r_max > 8) r_max = 8;
+    if (r_max < 1) r_max = 1;
     // a stage of about 24-32 KB; 2-bit boxes are whole 32-row blocks
     const int unit = p->g.format == PCAL_2BIT ? 32 : 8;
     int units = (28 * 1024) / (unit * cw * 4);
@@ -455,14 +455,29 @@ int bulk_tiling(const pcal_plan* p, int64_t n_rows, BulkTiling* t) {
     z.box_rows = box;
     const size_t stage = (size_t)box * cw * 4;
     const size_t stage_al = (stage + 1023) / 1024 * 1024;
+    // Box j lives in stage j % stages and is consumed by group j % r.  With
+    // stages a multiple of r every stage belongs to ONE group, which waits
+    // for its uses in order; otherwise a fast group could wait on a stage
+    // two phases ahead, where the mbarrier parity test would match an older
+    // phase (wrong tile, and arrivals beyond the barrier's count).
+    int r = 0, stages = 0;
+    for (int rr = r_max; rr >= 1 && r == 0; --rr) {
+        const size_t merge_rr = p->g.format == PCAL_2BIT ? (size_t)cw * 128
+                                : (p->g.format == PCAL_I8 ? (size_t)cw * 16 : (size_t)cw * rr * 8);
+        int st = (int)((kSmemBudget - merge_rr - 1024) / stage_al);
+        if (st > 8) st = 8;
+        st = st / rr * rr;
+        if (st < 3 || st < rr) continue;
+        // the 2-bit replica merge reuses the stage buffers as scratch
+        if (p->g.format == PCAL_2BIT && (size_t)rr * cw * 128 > (size_t)st * stage_al) continue;
+        r = rr;
+        stages = st;
+    }
+    if (r == 0) return -1;
+    z.replicas = r;
+    z.stages = stages;
     const size_t merge = p->g.format == PCAL_2BIT ? (size_t)cw * 128
                          : (p->g.format == PCAL_I8 ? (size_t)cw * 16 : (size_t)cw * r * 8);
-    int stages = (int)((kSmemBudget - merge - 1024) / stage_al);
-    if (stages > 8) stages = 8;
-    if (stages < 3) return -1;
-    // the 2-bit replica merge reuses the stage buffers as scratch
-    if (p->g.format == PCAL_2BIT && (size_t)r * cw * 128 > (size_t)stages * stage_al) return -1;
-    z.stages = stages;
     // row groups: one wave over the SMs, rows per CTA a multiple of the box
     // and small enough for 16-bit per-CTA counts
     int64_t gr = p->num_sms / gc;
@@ -573,4 +588,28 @@ cudaError_t launch_bulk(pcal_plan* p, const void* d_rows, int64_t n_rows, int64_
         p->stats.kernel_launches += 1;
     }
     return e;
+}
+
+extern "C" int pcal_bulk_tiling(double fs, double f_comb, double f_offset, int N, int sample_format, int num_sms,
+                                int64_t n_rows, pcal_tiling* out) {
+    if (!out || num_sms <= 0 || n_rows <= 0) return PCAL_EINVAL;
+    pcal_plan tmp;
+    memset(static_cast<void*>(&tmp), 0, sizeof(tmp));
+    int rc = pcal_plan_geometry(fs, f_comb, f_offset, N, sample_format, &tmp.g);
+    if (rc != PCAL_OK) return rc;
+    tmp.num_sms = num_sms;
+    BulkTiling t;
+    if (bulk_tiling(&tmp, n_rows, &t) != 0) return PCAL_EINVAL;
+    out->cols_total = t.cols_total;
+    out->col_width = t.col_width;
+    out->col_groups = t.col_groups;
+    out->replicas = t.replicas;
+    out->box_rows = t.box_rows;
+    out->stages = t.stages;
+    out->row_groups = t.row_groups;
+    out->rows_per_cta = t.rows_per_cta;
+    out->upper_planes = t.upper_planes;
+    out->threads = t.threads;
+    out->smem_bytes = (int64_t)t.smem_bytes;
+    return PCAL_OK;
 }

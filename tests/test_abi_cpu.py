@@ -104,3 +104,42 @@ def test_bitplane_arithmetic_on_host(tmp_path):
     r = subprocess.run([str(exe)], capture_output=True, text=True)
     assert r.returncode == 0, r.stdout + r.stderr
     assert r.stdout.strip().endswith("OK")
+
+
+TILING_CASES = [(fs, fc, fo, fmt) for fmt in (pcal.PCAL_2BIT, pcal.PCAL_I8, pcal.PCAL_F32)
+                for fs, fc, fo in [(64e6, 1e6, 10e3), (16e6, 1e6, 10e3), (16, 4, 1), (32e6, 1e6, 5e5),
+                                   (1024e6, 1e6, 10e3), (48e6, 1e6, 30e3), (256e6, 1e6, 10e3), (128e6, 1e6, 7e4),
+                                   (32e6, 1e6, 0)]]
+
+
+@pytest.mark.parametrize("fs,fc,fo,fmt", TILING_CASES)
+@pytest.mark.parametrize("num_sms", [152, 148, 1])
+@pytest.mark.parametrize("n_rows", [1, 17, 5000, 80000, 3_000_000])
+def test_bulk_tiling_invariants(lib, fs, fc, fo, fmt, num_sms, n_rows):
+    """Host check of every bulk launch's shape: the kernel relies on each of
+    these properties (bounds of the TMA boxes and shared memory, the 16-bit
+    per-CTA counters, whole 32-row 2-bit blocks, one consumer group per
+    pipeline stage, full coverage of the rows)."""
+    N = int(fs) // int(fc)
+    g = pcal.pcal_plan_geometry(fs, fc, fo, N, fmt)
+    try:
+        t = pcal.pcal_bulk_tiling(fs, fc, fo, N, fmt, num_sms, n_rows)
+    except pcal.PcalError:
+        pytest.fail("no tile plan")
+    spw = g.samples_per_byte_x4
+    assert t.cols_total == g.row_samples // spw
+    assert t.col_width % 8 == 0 and 8 <= t.col_width <= 256          # TMA box: <= 256, 32-byte rows
+    assert t.col_groups * t.col_width >= t.cols_total > (t.col_groups - 1) * t.col_width
+    assert 1 <= t.box_rows <= 256
+    if fmt == pcal.PCAL_2BIT:
+        assert t.box_rows % 32 == 0                                  # whole add32 blocks
+        rows_per_thread = -(-(t.rows_per_cta // t.box_rows) // t.replicas) * t.box_rows
+        assert rows_per_thread // 32 < (1 << t.upper_planes) or t.upper_planes == 0 and rows_per_thread < 32
+        assert t.upper_planes <= 11
+        assert t.replicas * t.col_width * 128 <= t.stages * ((t.box_rows * t.col_width * 4 + 1023) // 1024 * 1024)
+    assert t.stages % t.replicas == 0 and t.stages >= 3             # one consumer group per stage
+    assert t.rows_per_cta % t.box_rows == 0 and t.rows_per_cta <= 65535
+    assert t.row_groups * t.rows_per_cta >= n_rows > (t.row_groups - 1) * t.rows_per_cta
+    wpr = (t.col_width + 31) // 32
+    assert t.threads == (wpr * t.replicas + 1) * 32 <= 896
+    assert t.smem_bytes + 1024 <= 227 * 1024
