@@ -303,7 +303,17 @@ extern "C" int pcal_get_bins(pcal_plan* p, void* host_out) {
     cudaError_t e = cudaStreamSynchronize(p->last_stream);
     if (e != cudaSuccess) return cuda_status(e);
     if (p->g.format == PCAL_I8) return cuda_status(cudaMemcpy(host_out, p->d_acc8, L * 8, cudaMemcpyDeviceToHost));
-    if (p->g.format == PCAL_F32) return cuda_status(cudaMemcpy(host_out, p->d_accf, L * 8, cudaMemcpyDeviceToHost));
+    if (p->g.format == PCAL_F32) {
+        // double-float bins -> FP64 on the host
+        float* tmp = static_cast<float*>(malloc((size_t)L * 2 * sizeof(float)));
+        if (!tmp) return PCAL_ENOMEM;
+        e = cudaMemcpy(tmp, p->d_accf, (size_t)L * 2 * sizeof(float), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess)
+            for (int64_t k = 0; k < L; ++k)
+                static_cast<double*>(host_out)[k] = (double)tmp[2 * k] + (double)tmp[2 * k + 1];
+        free(tmp);
+        return cuda_status(e);
+    }
     void* d_tmp = nullptr;
     e = cudaMalloc(&d_tmp, (size_t)L * 4 * 8);
     if (e == cudaSuccess) e = launch_export_bins(p, d_tmp, p->last_stream);

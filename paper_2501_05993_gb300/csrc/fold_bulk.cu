@@ -32,11 +32,12 @@
 #include <cudaTypedefs.h>
 
 #include "bitplane.cuh"
+#include "df64.cuh"
 #include "internal.cuh"
 
 namespace {
 
-constexpr int kMaxBlock = 896;           // consumer warps + producer warp
+constexpr int kMaxBlock = 640;           // consumer warps + producer warp (<= 96 registers)
 constexpr int kSmemBudget = 220 * 1024;  // dynamic shared memory per CTA
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // give up a wait after 2 s
 
@@ -46,6 +47,7 @@ struct BulkArgs {
     int col_groups;   // G_c
     int replicas;     // r consumer groups
     int wpr;          // warps per group = ceil(col_width / 32)
+    int merge_stride; // words between merge rows (col_width rounded up, +2)
     int box_rows;     // rows per stage
     int stages;
     int consumers;    // C_w * r
@@ -163,8 +165,11 @@ struct AccF {
 //
 // Threads: `replicas` groups of `wpr` consumer warps, then one producer warp.
 // Lane c < col_width of a group owns column c0 + c; group q consumes the
-// boxes q, q + r, q + 2r, ... whole, so a box is read by one group only and
-// each group's warps release its stage with one arrival per warp.
+// boxes q, q + r, q + 2r, ... whole.  Box j lives in stage j % stages, and
+// stages is a multiple of r, so every stage belongs to one group, which
+// waits for its uses in order.  Every thread of the group arrives on the
+// stage's empty barrier once it holds the box's words in registers (2-bit)
+// or has folded them (int8, float32).
 template <int FMT, int U>
 __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                  const BulkArgs a) {
@@ -183,20 +188,15 @@ __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_co
 
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)a.stages * a.stage_stride);
     uint64_t* empty = full + a.stages;
-    uint8_t* merge = reinterpret_cast<uint8_t*>(empty + a.stages);
     __shared__ int s_failed;
 
     if (tid == 0) {
         s_failed = 0;
         for (int s = 0; s < a.stages; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], a.wpr);
+            mbar_init(&empty[s], group_threads);
         }
         fence_barrier_init();
-    }
-    {
-        const int words = FMT == PCAL_2BIT ? a.col_width * 32 : (FMT == PCAL_I8 ? a.col_width * 4 : 0);
-        for (int i = tid; i < words; i += blockDim.x) reinterpret_cast<uint32_t*>(merge)[i] = 0;
     }
     __syncthreads();
 
@@ -245,32 +245,38 @@ __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_co
                 break;
             }
             const uint32_t* p = reinterpret_cast<const uint32_t*>(smem + (size_t)s * a.stage_stride) + col;
-            if (active) {
-                if (FMT == PCAL_2BIT) {
-                    for (int b = 0; b < a.box_rows; b += 32) {
-                        uint32_t x[32];
+            if (FMT == PCAL_2BIT) {
+                for (int b = 0; b < a.box_rows; b += 32) {
+                    uint32_t x[32];
+                    if (active) {
 #pragma unroll
                         for (int i = 0; i < 32; ++i) x[i] = p[i * a.col_width];
-                        acc2.add32(x);
-                        p += 32 * a.col_width;
                     }
-                } else if (FMT == PCAL_I8) {
-#pragma unroll 8
-                    for (int i = 0; i < a.box_rows; ++i) acc8.add(p[i * a.col_width]);
-                } else {
-#pragma unroll 8
-                    for (int i = 0; i < a.box_rows; ++i) accf.add(p[i * a.col_width]);
+                    p += 32 * a.col_width;
+                    if (b + 32 >= a.box_rows) mbar_arrive(&empty[s]);  // words are in registers
+                    if (active) acc2.add32(x);
                 }
+            } else {
+                if (active) {
+                    if (FMT == PCAL_I8) {
+#pragma unroll 8
+                        for (int i = 0; i < a.box_rows; ++i) acc8.add(p[i * a.col_width]);
+                    } else {
+#pragma unroll 8
+                        for (int i = 0; i < a.box_rows; ++i) accf.add(p[i * a.col_width]);
+                    }
+                }
+                mbar_arrive(&empty[s]);
             }
-            __syncwarp();
-            if (tid % 32 == 0) mbar_arrive(&empty[s]);
         }
     }
     __syncthreads();
     if (s_failed) return;
 
     // ---------------- merge replicas, then flush ----------------
-    // The stage buffers are free now (every fill landed and was consumed).
+    // The stage buffers are free now (every fill landed and was consumed);
+    // they hold the merge scratch.  Layouts keep consecutive lanes on
+    // consecutive words (no bank conflicts).
     if (FMT == PCAL_2BIT) {
         uint32_t W[16], D[16];
 #pragma unroll
@@ -290,24 +296,26 @@ __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_co
             if (4 + u < 16) D[4 + u] = acc2.du[u];
         }
         // replicas add up pairwise in the bit-plane domain (ripple-carry adds
-        // of 16-plane numbers; per-CTA counts stay below 2^16)
+        // of 16-plane numbers; per-CTA counts stay below 2^16).
+        // scratch[(i*r + q)*C_w + col], i < 32 (16 w planes, 16 d planes)
         uint32_t* scratch = reinterpret_cast<uint32_t*>(smem);
+        const int rc = a.replicas * a.col_width;
         for (int step = 1; step < a.replicas; step <<= 1) {
             if (active && q % (2 * step) == step) {
-                uint32_t* dst = scratch + ((size_t)q * a.col_width + col) * 32;
+                uint32_t* dst = scratch + q * a.col_width + col;
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
-                    dst[i] = W[i];
-                    dst[16 + i] = D[i];
+                    dst[i * rc] = W[i];
+                    dst[(16 + i) * rc] = D[i];
                 }
             }
             __syncthreads();
             if (active && q % (2 * step) == 0 && q + step < a.replicas) {
-                const uint32_t* src = scratch + ((size_t)(q + step) * a.col_width + col) * 32;
+                const uint32_t* src = scratch + (q + step) * a.col_width + col;
                 uint32_t cw = 0, cd = 0;
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
-                    const uint32_t bw = src[i], bd = src[16 + i];
+                    const uint32_t bw = src[i * rc], bd = src[(16 + i) * rc];
                     const uint32_t sw = pcal_bits::lop3<pcal_bits::kXor3>(W[i], bw, cw);
                     cw = pcal_bits::lop3<pcal_bits::kMaj3>(W[i], bw, cw);
                     W[i] = sw;
@@ -318,51 +326,59 @@ __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_co
             }
             __syncthreads();
         }
+        // counts of column col: m[i*S + col], i < 32, S = a.merge_stride
+        uint32_t* m = scratch + 32 * rc;
         if (active && q == 0) {
             pcal_bits::transpose16x2(W);
             pcal_bits::transpose16x2(D);
-            uint32_t* m = reinterpret_cast<uint32_t*>(merge) + col * 32;
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
-                m[i] = W[i];
-                m[16 + i] = D[i];
+                m[i * a.merge_stride + col] = W[i];
+                m[(16 + i) * a.merge_stride + col] = D[i];
             }
         }
         __syncthreads();
+        // one atomic per (column, sample): consecutive threads, consecutive bins
+        const int S = a.merge_stride;
         const int tasks = a.col_width * 16;
         for (int t = tid; t < tasks; t += blockDim.x) {
             const int cl = t >> 4, j = t & 15;
             const int gc = c0 + cl;
             if (gc >= a.cols_total) continue;
-            const uint32_t* m = reinterpret_cast<const uint32_t*>(merge) + cl * 32;
             const int pl = 2 * j, ph = 2 * j + 1;  // bit positions of l and h
-            const uint32_t sl = (m[pl & 15] >> (16 * (pl >> 4))) & 0xFFFFu;
-            const uint32_t sh = (m[ph & 15] >> (16 * (ph >> 4))) & 0xFFFFu;
-            const uint32_t shl = ((m[16 + (pl & 15)] >> (16 * (pl >> 4))) & 0xFFFFu) +
-                                 ((m[16 + (ph & 15)] >> (16 * (ph >> 4))) & 0xFFFFu);
+            const uint32_t sl = (m[(pl & 15) * S + cl] >> (16 * (pl >> 4))) & 0xFFFFu;
+            const uint32_t sh = (m[(ph & 15) * S + cl] >> (16 * (ph >> 4))) & 0xFFFFu;
+            const uint32_t shl = ((m[(16 + (pl & 15)) * S + cl] >> (16 * (pl >> 4))) & 0xFFFFu) +
+                                 ((m[(16 + (ph & 15)) * S + cl] >> (16 * (ph >> 4))) & 0xFFFFu);
             if ((sl | sh) == 0) continue;
             const int64_t bin = (a.k_a + 16 * (int64_t)gc + j) % a.L;
             atomicAdd(&a.acc2[bin], (unsigned long long)sl | ((unsigned long long)sh << 21) |
                                          ((unsigned long long)shl << 42));
         }
     } else if (FMT == PCAL_I8) {
-        int* m = reinterpret_cast<int*>(merge);
+        // m[j*S + col], j < 4
+        int* m = reinterpret_cast<int*>(smem);
+        const int S = a.merge_stride;
+        for (int i = tid; i < 4 * S; i += blockDim.x) m[i] = 0;
+        __syncthreads();
         if (active) {
 #pragma unroll
             for (int j = 0; j < 4; ++j)
-                if (acc8.s[j]) atomicAdd(&m[col * 4 + j], acc8.s[j]);
+                if (acc8.s[j]) atomicAdd(&m[j * S + col], acc8.s[j]);
         }
         __syncthreads();
         for (int t = tid; t < a.col_width * 4; t += blockDim.x) {
-            const int gc = c0 + (t >> 2);
-            if (gc >= a.cols_total || m[t] == 0) continue;
-            const int64_t bin = (a.k_a + 4 * (int64_t)gc + (t & 3)) % a.L;
-            atomicAdd(reinterpret_cast<unsigned long long*>(&a.acc8[bin]), (unsigned long long)(long long)m[t]);
+            const int cl = t >> 2, j = t & 3;
+            const int gc = c0 + cl;
+            const int v = m[j * S + cl];
+            if (gc >= a.cols_total || v == 0) continue;
+            const int64_t bin = (a.k_a + 4 * (int64_t)gc + j) % a.L;
+            atomicAdd(reinterpret_cast<unsigned long long*>(&a.acc8[bin]), (unsigned long long)(long long)v);
         }
     } else {
         // f32: replicas in a fixed order, then one partial per column per
         // row group; a second kernel sums the partials per bin.
-        float2* m = reinterpret_cast<float2*>(merge);
+        float2* m = reinterpret_cast<float2*>(smem);
         if (active) m[q * a.col_width + col] = make_float2(accf.s, accf.c);
         __syncthreads();
         if (tid < a.col_width && c0 + tid < a.cols_total) {
@@ -379,20 +395,22 @@ __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_co
 }
 
 // f32: bin k = sum over row groups and over the columns that map to k, in a
-// fixed order, added to the plan's FP64 bins.
+// fixed order and in double-float, added to the plan's double-float bins.
 __global__ void reduce_f32_kernel(const float2* __restrict__ part, int64_t row_groups, int cols_total, int64_t k_a,
-                                  int64_t L, double* __restrict__ acc) {
+                                  int64_t L, float2* __restrict__ acc) {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= L) return;
     const int64_t c_first = ((k - k_a) % L + L) % L;
     if (c_first >= cols_total) return;
-    double s = 0.0;
+    pcal_df::df s{0.f, 0.f};
     for (int64_t rg = 0; rg < row_groups; ++rg)
         for (int64_t c = c_first; c < cols_total; c += L) {
             const float2 v = part[rg * cols_total + c];
-            s += (double)v.x + (double)v.y;
+            s = pcal_df::add(s, pcal_df::two_sum(v.x, v.y));
         }
-    acc[k] += s;
+    const float2 a = acc[k];
+    s = pcal_df::add(pcal_df::df{a.x, a.y}, s);
+    acc[k] = make_float2(s.hi, s.lo);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
@@ -461,23 +479,23 @@ int bulk_tiling(const pcal_plan* p, int64_t n_rows, BulkTiling* t) {
     // two phases ahead, where the mbarrier parity test would match an older
     // phase (wrong tile, and arrivals beyond the barrier's count).
     int r = 0, stages = 0;
+    const int ms = (cw + 31) / 32 * 32 + 2;  // merge stride
     for (int rr = r_max; rr >= 1 && r == 0; --rr) {
-        const size_t merge_rr = p->g.format == PCAL_2BIT ? (size_t)cw * 128
-                                : (p->g.format == PCAL_I8 ? (size_t)cw * 16 : (size_t)cw * rr * 8);
-        int st = (int)((kSmemBudget - merge_rr - 1024) / stage_al);
+        int st = (int)((kSmemBudget - 1024) / stage_al);
         if (st > 8) st = 8;
         st = st / rr * rr;
         if (st < 3 || st < rr) continue;
-        // the 2-bit replica merge reuses the stage buffers as scratch
-        if (p->g.format == PCAL_2BIT && (size_t)rr * cw * 128 > (size_t)st * stage_al) continue;
+        // after the main loop the stage buffers hold the merge scratch
+        const size_t need = p->g.format == PCAL_2BIT ? (size_t)128 * rr * cw + (size_t)128 * ms
+                            : (p->g.format == PCAL_I8 ? (size_t)16 * ms : (size_t)8 * rr * cw);
+        if (need > (size_t)st * stage_al) continue;
         r = rr;
         stages = st;
     }
     if (r == 0) return -1;
     z.replicas = r;
     z.stages = stages;
-    const size_t merge = p->g.format == PCAL_2BIT ? (size_t)cw * 128
-                         : (p->g.format == PCAL_I8 ? (size_t)cw * 16 : (size_t)cw * r * 8);
+    z.merge_stride = ms;
     // row groups: one wave over the SMs, rows per CTA a multiple of the box
     // and small enough for 16-bit per-CTA counts
     int64_t gr = p->num_sms / gc;
@@ -496,7 +514,7 @@ int bulk_tiling(const pcal_plan* p, int64_t n_rows, BulkTiling* t) {
         z.upper_planes = bits_for(rows_per_thread / 32);
     }
     z.threads = (wpr * r + 1) * 32;
-    z.smem_bytes = (size_t)stages * stage_al + 16 * (size_t)stages + merge;
+    z.smem_bytes = (size_t)stages * stage_al + 16 * (size_t)stages;
     *t = z;
     return 0;
 }
@@ -535,6 +553,7 @@ cudaError_t launch_bulk(pcal_plan* p, const void* d_rows, int64_t n_rows, int64_
     a.col_groups = t.col_groups;
     a.replicas = t.replicas;
     a.wpr = (t.col_width + 31) / 32;
+    a.merge_stride = t.merge_stride;
     a.box_rows = t.box_rows;
     a.stages = t.stages;
     a.consumers = a.wpr * 32 * t.replicas;

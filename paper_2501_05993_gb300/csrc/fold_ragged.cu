@@ -6,6 +6,7 @@
 // and inputs too short for the bulk kernel.  2-bit and int8 bins are exact
 // integers, so atomic order does not matter; float32 bins are summed by one
 // thread per bin in sample order, so they are deterministic.
+#include "df64.cuh"
 #include "internal.cuh"
 
 namespace {
@@ -38,15 +39,18 @@ __global__ void ragged_i8_kernel(const int8_t* __restrict__ x, int64_t n, int64_
 }
 
 // One thread per bin k: sums the samples of this run that fall into bin k, in
-// order, and adds the sum to the plan's FP64 bin.
+// order, in double-float, and adds the sum to the plan's double-float bin.
 __global__ void ragged_f32_kernel(const float* __restrict__ x, int64_t n, int64_t k0, int64_t L,
-                                  double* __restrict__ acc) {
+                                  float2* __restrict__ acc) {
     int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= L) return;
     int64_t t = (k - k0 % L + L) % L;  // first sample index of this run in bin k
-    double s = 0.0;
-    for (; t < n; t += L) s += (double)x[t];
-    if (s != 0.0) acc[k] += s;
+    if (t >= n) return;
+    pcal_df::df s{0.f, 0.f};
+    for (; t < n; t += L) s = pcal_df::add_f(s, x[t]);
+    const float2 a = acc[k];
+    s = pcal_df::add(pcal_df::df{a.x, a.y}, s);
+    acc[k] = make_float2(s.hi, s.lo);
 }
 
 // Move the packed 21-bit fields into the wide 64-bit arrays and clear them.

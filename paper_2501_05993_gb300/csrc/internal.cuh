@@ -32,6 +32,7 @@ struct BulkTiling {
     int64_t rows_per_cta;    // multiple of box_rows
     int upper_planes;  // 2-bit: bit planes above the Harley-Seal tree
     int threads;       // consumer threads + 1 producer warp
+    int merge_stride;  // words between rows of the end-of-tile merge area
     size_t smem_bytes;
 };
 
@@ -59,7 +60,7 @@ struct pcal_plan {
     unsigned long long* d_acc2;   // 2-bit packed counts [L]
     unsigned long long* d_wide2;  // 2-bit spilled counts [3][L]
     long long* d_acc8;            // int8 sums [L]
-    double* d_accf;               // float32 sums (FP64) [L]
+    float2* d_accf;               // float32 sums as double-float (hi, lo) [L]
     float2* d_partf;              // float32 per-tile partial sums (scratch)
     size_t partf_cap;             // capacity of d_partf in float2
     double2* d_tw;                // exp(-j 2 pi m / L), m < L

@@ -136,10 +136,21 @@ def test_bulk_tiling_invariants(lib, fs, fc, fo, fmt, num_sms, n_rows):
         rows_per_thread = -(-(t.rows_per_cta // t.box_rows) // t.replicas) * t.box_rows
         assert rows_per_thread // 32 < (1 << t.upper_planes) or t.upper_planes == 0 and rows_per_thread < 32
         assert t.upper_planes <= 11
-        assert t.replicas * t.col_width * 128 <= t.stages * ((t.box_rows * t.col_width * 4 + 1023) // 1024 * 1024)
+        ms = (t.col_width + 31) // 32 * 32 + 2
+        assert t.replicas * t.col_width * 128 + 128 * ms <= t.stages * ((t.box_rows * t.col_width * 4 + 1023) // 1024 * 1024)
     assert t.stages % t.replicas == 0 and t.stages >= 3             # one consumer group per stage
     assert t.rows_per_cta % t.box_rows == 0 and t.rows_per_cta <= 65535
     assert t.row_groups * t.rows_per_cta >= n_rows > (t.row_groups - 1) * t.rows_per_cta
     wpr = (t.col_width + 31) // 32
-    assert t.threads == (wpr * t.replicas + 1) * 32 <= 896
+    assert t.threads == (wpr * t.replicas + 1) * 32 <= 640
     assert t.smem_bytes + 1024 <= 227 * 1024
+
+
+def test_double_float_arithmetic_on_host(tmp_path):
+    exe = tmp_path / "df64_check"
+    src = os.path.join(ROOT, "tests", "host", "df64_check.cpp")
+    inc = os.path.join(ROOT, "paper_2501_05993_gb300", "csrc")
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-I", inc, src, "-o", str(exe)])
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert r.stdout.strip().endswith("OK")
