@@ -50,6 +50,36 @@ def rank_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def reduce_max(x: float, dist, device: str) -> float:
+    """Maximum of a per-rank scalar over all ranks (identity without dist)."""
+    if dist is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(world: int, samples_per_rank_step: int, steps: int, total_ms: float) -> float:
+    """Whole-job throughput in Gsamples/s: every rank's samples over the
+    slowest rank's time."""
+    return world * samples_per_rank_step * steps / (total_ms / 1e3) / 1e9
+
+
+def shard_range(n_total: int, world: int, rank: int, quantum: int = 4):
+    """Contiguous share [start, start+count) of a stream of n_total samples for
+    `rank`, in whole quanta (4 samples = one 2-bit byte).  A rank folds its
+    share starting at absolute index `start`; the exact integer bins of all
+    shares add up to those of the whole stream."""
+    units = n_total // quantum
+    lo = units * rank // world
+    hi = units * (rank + 1) // world
+    start = lo * quantum
+    count = (hi - lo) * quantum + (n_total - units * quantum if rank == world - 1 else 0)
+    return start, count
+
+
 def read_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -250,11 +280,8 @@ def run_gpu(args):
     total_ms = t_start.elapsed_time(t_end)
     fold_ms = statistics.mean(e0.elapsed_time(e1) for e0, e1, _ in ev)
     fin_ms = statistics.mean(e1.elapsed_time(e2) for _, e1, e2 in ev)
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * M * args.steps / (total_ms / 1e3) / 1e9
+    total_ms = reduce_max(total_ms, dist, "cuda")
+    value = aggregate_value(world, M, args.steps, total_ms)
 
     res = plan.results()
 
@@ -275,12 +302,8 @@ def run_gpu(args):
             plan.accumulate_host(ph, M, stream)
             plan.finalize()  # device -> host read of the phasors, synchronising
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([dt], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": world * M * k_e2e / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+        dt = reduce_max(time.perf_counter() - t0, dist, "cuda")
+        e2e = {"value": aggregate_value(world, M, k_e2e, dt * 1e3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": (5 * N_TONES + 3) * 8, "steps": k_e2e}
 
     peak, peak_kind = read_peaks()

@@ -111,7 +111,7 @@ def test_bins_and_phasors(pcal, fmt, plan_name, n_case):
         res = p.results()
     S = oracle.bins(host, fmt, 0, p.L)
     check_phasors(T, oracle.tones_from_bins(S, fs, fc, fo))
-    assert np.allclose(res["amp"], 2 * np.abs(T) / n, rtol=1e-12)
+    assert np.allclose(res["amp"], 2 * np.abs(T) / n, rtol=1e-6)  # FP32 amplitudes
 
 
 @pytest.mark.parametrize("fmt", ["2bit", "i8", "f32"])
