@@ -207,9 +207,10 @@ int pcal_get_stats(const pcal_plan* plan, pcal_stats* out);
  */
 typedef struct {
     int32_t cols_total, col_width, col_groups, replicas, box_rows, stages;
-    int64_t row_groups, rows_per_cta;
+    int64_t row_groups, rows_per_cta;   /* CTAs per column group; most rows one CTA folds */
     int32_t upper_planes, threads;
     int64_t smem_bytes;
+    int32_t total_boxes, static_boxes, max_boxes;  /* per column group; per CTA */
 } pcal_tiling;
 
 int pcal_bulk_tiling(double fs, double f_comb, double f_offset, int N, int sample_format, int num_sms,

@@ -47,7 +47,8 @@ class Tiling(ctypes.Structure):
     _fields_ = [("cols_total", ctypes.c_int32), ("col_width", ctypes.c_int32), ("col_groups", ctypes.c_int32),
                 ("replicas", ctypes.c_int32), ("box_rows", ctypes.c_int32), ("stages", ctypes.c_int32),
                 ("row_groups", ctypes.c_int64), ("rows_per_cta", ctypes.c_int64), ("upper_planes", ctypes.c_int32),
-                ("threads", ctypes.c_int32), ("smem_bytes", ctypes.c_int64)]
+                ("threads", ctypes.c_int32), ("smem_bytes", ctypes.c_int64), ("total_boxes", ctypes.c_int32),
+                ("static_boxes", ctypes.c_int32), ("max_boxes", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

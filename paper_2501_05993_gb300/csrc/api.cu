@@ -35,6 +35,7 @@ void free_plan(pcal_plan* p) {
     cudaFree(p->d_res);
     cudaFree(p->d_ticket);
     cudaFree(p->d_err);
+    cudaFree(p->d_sched);
     for (int i = 0; i < 2; ++i) {
         cudaFree(p->d_stage[i]);
         if (p->stage_ev[i]) cudaEventDestroy(p->stage_ev[i]);
@@ -134,6 +135,7 @@ extern "C" int pcal_plan_create(double fs, double f_comb, double f_offset, int N
     if (e == cudaSuccess) e = dalloc(&p->d_res, 5 * Nn + 3);
     if (e == cudaSuccess) e = dalloc(&p->d_ticket, 4);
     if (e == cudaSuccess) e = dalloc(&p->d_err, 4);
+    if (e == cudaSuccess) e = dalloc(&p->d_sched, kSchedCounters + 1);
     if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&p->h_res), (5 * Nn + 3) * sizeof(double));
     if (e == cudaSuccess) e = launch_init_twiddles(p, 0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(0);

@@ -80,13 +80,22 @@ PCAL_HD df mul_f(df x, float y) {
     return quick_two_sum(p.hi, p.lo);
 }
 
-// x / y by two correction steps of the float quotient.
+// Approximate float quotient; the df steps below correct its error.
+PCAL_HD float fdiv_approx(float a, float b) {
+#if defined(__CUDA_ARCH__)
+    return __fdividef(a, b);
+#else
+    return a / b;
+#endif
+}
+
+// x / y by two correction steps of an approximate float quotient.
 PCAL_HD df div(df x, df y) {
-    const float q1 = x.hi / y.hi;
+    const float q1 = fdiv_approx(x.hi, y.hi);
     df r = sub(x, mul_f(y, q1));
-    const float q2 = r.hi / y.hi;
+    const float q2 = fdiv_approx(r.hi, y.hi);
     r = sub(r, mul_f(y, q2));
-    const float q3 = r.hi / y.hi;
+    const float q3 = fdiv_approx(r.hi, y.hi);
     return add_f(quick_two_sum(q1, q2), q3);
 }
 
@@ -95,7 +104,7 @@ PCAL_HD df sqrt_df(df x) {
     if (!(x.hi > 0.0f)) return df{0.0f, 0.0f};
     const float s = sqrtf(x.hi);
     const df r = sub(x, two_prod(s, s));
-    return quick_two_sum(s, r.hi / (2.0f * s));
+    return quick_two_sum(s, fdiv_approx(r.hi, 2.0f * s));
 }
 
 }  // namespace pcal_df

@@ -87,6 +87,11 @@ __device__ __forceinline__ double take_bin(const FinArgs& a, int64_t k) {
     return (double)v.x + (double)v.y;
 }
 
+// Programmatic dependent launch: wait for the preceding kernel's results;
+// allow the following kernel to start launching.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ df df_of(double x) {
     const float hi = (float)x;
     return df{hi, (float)(x - (double)hi)};
@@ -141,14 +146,16 @@ __device__ __forceinline__ float wrap_pi_f(float x) {
     return x - 6.283185307179586f * floorf((x + 3.141592653589793f) * 0.15915494309189535f);
 }
 
-// Tones [i0, i1) of the N-point DFT of P, in FP32.  Groups of g threads (a
-// power of two <= 32) share a tone and combine their partial sums with a
-// fixed butterfly.
-__device__ void dft_tones(const FinArgs& a, int64_t i0, int64_t i1, float2* sP) {
+// Tones [i0, i1) of the N-point DFT of P, in FP32, written to global T and,
+// when sT is given, to shared memory.  P (hi + lo) and the twiddles are
+// staged in shared memory first.  Groups of g threads (a power of two <= 32)
+// share a tone and combine their partial sums with a fixed butterfly.
+__device__ void dft_tones(const FinArgs& a, int64_t i0, int64_t i1, float2* sP, float2* sTw, float2* sT) {
     const int64_t N = a.N;
     for (int64_t b = threadIdx.x; b < N; b += blockDim.x) {
         const float4 v = __ldcg(&a.P[b]);
         sP[b] = make_float2(v.x + v.y, v.z + v.w);
+        sTw[b] = a.twN[b];
     }
     __syncthreads();
     const int64_t ntone = i1 - i0;
@@ -160,117 +167,144 @@ __device__ void dft_tones(const FinArgs& a, int64_t i0, int64_t i1, float2* sP) 
         const int64_t i = i0 + base + threadIdx.x / g;
         float re = 0.f, im = 0.f;
         if (i < i1) {
-            int64_t idx = (i * sub) % N;
-            const int64_t step = (i * g) % N;
-            for (int64_t b = sub; b < N; b += g) {
+            int idx = (int)((i * sub) % N);
+            const int step = (int)((i * g) % N);
+            const int n = (int)N;
+            for (int b = sub; b < n; b += g) {
                 const float2 p = sP[b];
-                const float2 w = a.twN[idx];
+                const float2 w = sTw[idx];
                 re = fmaf(p.x, w.x, fmaf(-p.y, w.y, re));
                 im = fmaf(p.x, w.y, fmaf(p.y, w.x, im));
                 idx += step;
-                if (idx >= N) idx -= N;
+                if (idx >= n) idx -= n;
             }
         }
         for (int o = g / 2; o > 0; o >>= 1) {
             re += __shfl_xor_sync(0xffffffffu, re, o);
             im += __shfl_xor_sync(0xffffffffu, im, o);
         }
-        if (i < i1 && sub == 0) a.T[i] = make_float2(re, im);
+        if (i < i1 && sub == 0) {
+            a.T[i] = make_float2(re, im);
+            if (sT) sT[i] = make_float2(re, im);
+        }
     }
     __syncthreads();
 }
 
-// Shared memory of tone_products: psi[N] floats, un[N] float2, then 96
-// float2 of reduction scratch.
-__host__ __device__ size_t products_smem(int64_t N) {
-    return (size_t)((N * 4 + 15) / 16) * 16 + (size_t)N * 8 + 96 * 8;
+// Shared memory of the products: T[N] float2, psi[N] float, un[N] float2,
+// then reduction scratch (96 float2) and the two df results.
+struct ProductsSmem {
+    float2* T;
+    float* psi;
+    float2* un;
+    float2* red;
+    float2* out;  // [0] td (df), [1] sigma (df)
+};
+
+__host__ __device__ inline size_t products_bytes(int64_t N) {
+    return (size_t)N * 8 + (size_t)((N * 4 + 15) / 16) * 16 + (size_t)N * 8 + 98 * 8;
+}
+
+__device__ inline ProductsSmem products_layout(uint8_t* base, int64_t N) {
+    ProductsSmem m;
+    m.T = reinterpret_cast<float2*>(base);
+    m.psi = reinterpret_cast<float*>(base + N * 8);
+    m.un = reinterpret_cast<float2*>(base + N * 8 + ((N * 4 + 15) / 16) * 16);
+    m.red = m.un + N;
+    m.out = m.red + 96;
+    return m;
 }
 
 // Amplitude, phase, unwrapped phase and the weighted LS delay fit over all N
-// tones; one CTA, after every T_i is in global memory.
-__device__ void tone_products(const FinArgs& a, uint8_t* smem) {
+// tones, from T in shared memory; one CTA.  The first nt threads (whole
+// warps, about 8 tones each) do the arithmetic; all threads then write the
+// FP64 results.
+__device__ void tone_products(const FinArgs& a, const ProductsSmem& m) {
     const int64_t N = a.N;
-    const int nt = blockDim.x, t = threadIdx.x;
-    float* psi = reinterpret_cast<float*>(smem);
-    float2* un = reinterpret_cast<float2*>(smem + ((N * 4 + 15) / 16) * 16);
-    float2* red = un + N;
+    const int t = threadIdx.x;
+    int nt = (int)((N + 7) / 8 + 31) / 32 * 32;
+    if (nt > (int)blockDim.x) nt = blockDim.x;
     const int64_t chunk = (N + nt - 1) / nt;
-    const int64_t c0 = t * chunk < N ? t * chunk : N;
+    const int64_t c0 = t < nt ? (t * chunk < N ? t * chunk : N) : N;
     const int64_t c1 = c0 + chunk < N ? c0 + chunk : N;
-    double* amp = a.res + 2 * N;
-    double* ph = a.res + 3 * N;
-    double* unw = a.res + 4 * N;
-    // 1. per tone, FP32
+    // 1. phase per tone, FP32
     for (int64_t i = c0; i < c1; ++i) {
-        const float2 z = __ldcg(&a.T[i]);
-        const float p = wrap_pi_f(atan2f(z.y, z.x) + 1.5707963267948966f);
-        psi[i] = p;
-        a.res[2 * i] = (double)z.x;
-        a.res[2 * i + 1] = (double)z.y;
-        amp[i] = (double)(sqrtf(z.x * z.x + z.y * z.y) * a.two_over_m);
-        ph[i] = (double)p;
+        const float2 z = m.T[i];
+        m.psi[i] = wrap_pi_f(atan2f(z.y, z.x) + 1.5707963267948966f);
     }
     __syncthreads();
     // 2. unwrap: u_i = psi_0 + sum_{j=1..i} wrap(psi_j - psi_{j-1}), df sums
     df local{0.f, 0.f};
     for (int64_t i = c0; i < c1; ++i)
-        if (i > 0) local = pcal_df::add_f(local, wrap_pi_f(psi[i] - psi[i - 1]));
-    df run = pcal_df::add_f(block_exclusive_scan_df(local, red), psi[0]);
+        if (i > 0) local = pcal_df::add_f(local, wrap_pi_f(m.psi[i] - m.psi[i - 1]));
+    df run = pcal_df::add_f(block_exclusive_scan_df(local, m.red), m.psi[0]);
     for (int64_t i = c0; i < c1; ++i) {
-        if (i > 0) run = pcal_df::add_f(run, wrap_pi_f(psi[i] - psi[i - 1]));
-        un[i] = make_float2(run.hi, run.lo);
-        unw[i] = (double)run.hi + (double)run.lo;
+        if (i > 0) run = pcal_df::add_f(run, wrap_pi_f(m.psi[i] - m.psi[i - 1]));
+        m.un[i] = make_float2(run.hi, run.lo);
     }
-    __syncthreads();
     // 3. weighted least squares of u_i against the tone index x_i = i (the
     //    frequency is f_i = f_comb*i + f_offset), weights w_i = |T_i|^2
     df s3[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     for (int64_t i = c0; i < c1; ++i) {
-        const float2 z = __ldcg(&a.T[i]);
+        const float2 z = m.T[i];
         const float w = z.x * z.x + z.y * z.y;
         s3[0] = pcal_df::add_f(s3[0], w);
         s3[1] = pcal_df::add(s3[1], pcal_df::two_prod(w, (float)i));
-        s3[2] = pcal_df::add(s3[2], pcal_df::mul_f(df{un[i].x, un[i].y}, w));
+        s3[2] = pcal_df::add(s3[2], pcal_df::mul_f(df{m.un[i].x, m.un[i].y}, w));
     }
-    block_sums_df<3>(s3, red);
+    block_sums_df<3>(s3, m.red);
     const df W = s3[0];
-    double td = nan(""), sig = nan("");
+    df td{__int_as_float(0x7fc00000), 0.f}, sig{__int_as_float(0x7fc00000), 0.f};  // NaN until fitted
     if (N >= 2 && W.hi > 0.f) {
         const df xbar = pcal_df::div(s3[1], W), ubar = pcal_df::div(s3[2], W);
         df s2[2] = {{0.f, 0.f}, {0.f, 0.f}};
         for (int64_t i = c0; i < c1; ++i) {
-            const float2 z = __ldcg(&a.T[i]);
+            const float2 z = m.T[i];
             const float w = z.x * z.x + z.y * z.y;
             const df dx = pcal_df::sub(df{(float)i, 0.f}, xbar);
-            const df du = pcal_df::sub(df{un[i].x, un[i].y}, ubar);
+            const df du = pcal_df::sub(df{m.un[i].x, m.un[i].y}, ubar);
             const df wdx = pcal_df::mul_f(dx, w);
             s2[0] = pcal_df::add(s2[0], pcal_df::mul(wdx, dx));
             s2[1] = pcal_df::add(s2[1], pcal_df::mul(wdx, du));
         }
-        block_sums_df<2>(s2, red);
+        block_sums_df<2>(s2, m.red);
         if (s2[0].hi > 0.f) {
             const df slope = pcal_df::div(s2[1], s2[0]);  // rad per tone index
             df s1[1] = {{0.f, 0.f}};
             for (int64_t i = c0; i < c1; ++i) {
-                const float2 z = __ldcg(&a.T[i]);
+                const float2 z = m.T[i];
                 const float w = z.x * z.x + z.y * z.y;
                 const df dx = pcal_df::sub(df{(float)i, 0.f}, xbar);
-                const df r = pcal_df::sub(pcal_df::sub(df{un[i].x, un[i].y}, ubar), pcal_df::mul(slope, dx));
+                const df r = pcal_df::sub(pcal_df::sub(df{m.un[i].x, m.un[i].y}, ubar), pcal_df::mul(slope, dx));
                 s1[0] = pcal_df::add(s1[0], pcal_df::mul_f(pcal_df::mul(r, r), w));
             }
-            block_sums_df<1>(s1, red);
-            const df tdd = pcal_df::div(slope, a.two_pi_fc);
-            td = (double)tdd.hi + (double)tdd.lo;
-            if (N > 2) {
-                const df v = pcal_df::div(pcal_df::div(s1[0], df{(float)(N - 2), 0.f}), s2[0]);
-                const df sd = pcal_df::div(pcal_df::sqrt_df(v), a.two_pi_fc);
-                sig = (double)sd.hi + (double)sd.lo;
-            }
+            block_sums_df<1>(s1, m.red);
+            td = pcal_df::div(slope, a.two_pi_fc);
+            if (N > 2)
+                sig = pcal_df::div(pcal_df::sqrt_df(pcal_df::div(pcal_df::div(s1[0], df{(float)(N - 2), 0.f}), s2[0])),
+                                   a.two_pi_fc);
         }
     }
     if (t == 0) {
-        a.res[5 * N] = td;
-        a.res[5 * N + 1] = sig;
+        m.out[0] = make_float2(td.hi, td.lo);
+        m.out[1] = make_float2(sig.hi, sig.lo);
+    }
+    __syncthreads();
+    // 4. FP64 results, written by all threads
+    double* amp = a.res + 2 * N;
+    double* ph = a.res + 3 * N;
+    double* unw = a.res + 4 * N;
+    for (int64_t i = t; i < N; i += blockDim.x) {
+        const float2 z = m.T[i];
+        a.res[2 * i] = (double)z.x;
+        a.res[2 * i + 1] = (double)z.y;
+        amp[i] = (double)(sqrtf(z.x * z.x + z.y * z.y) * a.two_over_m);
+        ph[i] = (double)m.psi[i];
+        unw[i] = (double)m.un[i].x + (double)m.un[i].y;
+    }
+    if (t == 0) {
+        a.res[5 * N] = (double)m.out[0].x + (double)m.out[0].y;
+        a.res[5 * N + 1] = (double)m.out[1].x + (double)m.out[1].y;
         a.res[5 * N + 2] = a.M;
     }
 }
@@ -282,6 +316,8 @@ __device__ void tone_products(const FinArgs& a, uint8_t* smem) {
 __global__ void fin_fold_kernel(FinArgs a) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ bool is_last;
+    grid_dependency_wait();  // the bins of the preceding fold
+    allow_dependents();
     const int tpb = a.tpb;
     const int bl = threadIdx.x / tpb, sub = threadIdx.x % tpb;
     const int64_t b = (int64_t)blockIdx.x * a.bc + bl;
@@ -328,9 +364,11 @@ __global__ void fin_fold_kernel(FinArgs a) {
     __threadfence();
     if (threadIdx.x == 0) a.ticket[0] = 0;
     if (a.N <= kDftInFoldMaxN) {
-        dft_tones(a, 0, a.N, reinterpret_cast<float2*>(smem));
-        __threadfence();
-        tone_products(a, smem);
+        // shared memory: products area, then P and the twiddles for the DFT
+        const ProductsSmem m = products_layout(smem, a.N);
+        float2* sP = reinterpret_cast<float2*>(smem + products_bytes(a.N));
+        dft_tones(a, 0, a.N, sP, sP + a.N, m.T);
+        tone_products(a, m);
     }
 }
 
@@ -338,9 +376,12 @@ __global__ void fin_fold_kernel(FinArgs a) {
 __global__ void fin_dft_kernel(FinArgs a) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ bool is_last;
+    grid_dependency_wait();  // P of the fold kernel
+    allow_dependents();
     const int64_t i0 = (int64_t)blockIdx.x * kDftTonesPerCta;
     const int64_t i1 = i0 + kDftTonesPerCta < a.N ? i0 + kDftTonesPerCta : a.N;
-    dft_tones(a, i0, i1, reinterpret_cast<float2*>(smem));
+    float2* sP = reinterpret_cast<float2*>(smem);
+    dft_tones(a, i0, i1, sP, sP + a.N, nullptr);
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) is_last = atomicAdd(&a.ticket[1], 1u) == gridDim.x - 1;
@@ -348,7 +389,10 @@ __global__ void fin_dft_kernel(FinArgs a) {
     if (!is_last) return;
     __threadfence();
     if (threadIdx.x == 0) a.ticket[1] = 0;
-    tone_products(a, smem);
+    const ProductsSmem m = products_layout(smem, a.N);
+    for (int64_t i = threadIdx.x; i < a.N; i += blockDim.x) m.T[i] = __ldcg(&a.T[i]);
+    __syncthreads();
+    tone_products(a, m);
 }
 
 __global__ void init_twiddles_kernel(double2* tw, int64_t L, float2* twN, int64_t N, int64_t sc) {
@@ -358,6 +402,22 @@ __global__ void init_twiddles_kernel(double2* tw, int64_t L, float2* twN, int64_
         tw[m] = make_double2(c, -s);
         if (m % sc == 0 && m / sc < N) twN[m / sc] = make_float2((float)c, (float)-s);
     }
+}
+
+// Launch as a programmatic dependent of the preceding kernel in the stream.
+template <typename... Args>
+cudaError_t launch_pdl(void (*k)(Args...), int grid, int block, size_t smem, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, args...);
 }
 
 }  // namespace
@@ -413,7 +473,7 @@ cudaError_t launch_finalize(pcal_plan* p, cudaStream_t s) {
     const int threads = (a.bc * a.tpb + 31) / 32 * 32;
     size_t smem = (size_t)threads * 16;
     if (g.N <= kDftInFoldMaxN) {
-        const size_t need = products_smem(g.N) > (size_t)g.N * 8 ? products_smem(g.N) : (size_t)g.N * 8;
+        const size_t need = products_bytes(g.N) + (size_t)g.N * 16;  // products + P + twiddles
         if (need > smem) smem = need;
     }
     cudaError_t e = cudaSuccess;
@@ -423,19 +483,18 @@ cudaError_t launch_finalize(pcal_plan* p, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         fold_smem_set = smem;
     }
-    fin_fold_kernel<<<G, threads, smem, s>>>(a);
+    e = launch_pdl(fin_fold_kernel, G, threads, smem, s, a);
     p->stats.kernel_launches += 1;
-    e = cudaGetLastError();
     if (e != cudaSuccess || g.N <= kDftInFoldMaxN) return e;
     const int threads2 = 256;
-    const size_t smem2 = (size_t)g.N * 8 > products_smem(g.N) ? (size_t)g.N * 8 : products_smem(g.N);
+    const size_t smem2 = (size_t)g.N * 16 > products_bytes(g.N) ? (size_t)g.N * 16 : products_bytes(g.N);
     static size_t dft_smem_set = 0;
     if (smem2 > 48 * 1024 && smem2 > dft_smem_set) {
         e = cudaFuncSetAttribute(fin_dft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
         if (e != cudaSuccess) return e;
         dft_smem_set = smem2;
     }
-    fin_dft_kernel<<<(unsigned)((g.N + kDftTonesPerCta - 1) / kDftTonesPerCta), threads2, smem2, s>>>(a);
+    e = launch_pdl(fin_dft_kernel, (int)((g.N + kDftTonesPerCta - 1) / kDftTonesPerCta), threads2, smem2, s, a);
     p->stats.kernel_launches += 1;
-    return cudaGetLastError();
+    return e;
 }

@@ -53,7 +53,13 @@ struct BulkArgs {
     int consumers;    // C_w * r
     uint32_t stage_stride;  // bytes between stages (1024-aligned)
     uint32_t tx_bytes;      // bytes one TMA box delivers
-    int64_t rows_per_cta;
+    int total_boxes;  // boxes per column group
+    int row_groups;   // CTAs per column group
+    int static_boxes; // boxes each CTA takes without the shared counter
+    int max_boxes;    // cap per CTA (keeps per-CTA counts below 2^16)
+    int chunk;        // boxes per grab from the shared counter
+    unsigned int* sched;  // per column group: boxes handed out dynamically
+    unsigned int* done;   // CTAs finished; the last one resets sched
     int64_t n_rows;
     int64_t k_a;      // phase of the first sample of row 0
     int64_t L;
@@ -84,6 +90,11 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                  : "memory");
 }
+
+// Programmatic dependent launch: wait for the preceding kernel's results;
+// allow the following kernel to start launching.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // try_wait suspends the thread in hardware for a while instead of spinning.
 __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
@@ -160,6 +171,20 @@ struct AccF {
     }
 };
 
+// The last CTA of a launch to finish resets the dynamic box counters for the
+// next launch (stream order makes the reset visible to it).
+__device__ void finish_cta(const BulkArgs& a) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(a.done, 1u) == gridDim.x - 1) {
+            for (int g = 0; g < a.col_groups; ++g) a.sched[g] = 0;
+            *a.done = 0;
+            __threadfence();
+        }
+    }
+}
+
 // ---- the kernel ------------------------------------------------------------------
 // FMT: PCAL_2BIT, PCAL_I8 or PCAL_F32.  U: upper bit planes (2-bit only).
 //
@@ -181,20 +206,22 @@ __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_co
     const int cg = blockIdx.x % a.col_groups;
     const int64_t rg = blockIdx.x / a.col_groups;
     const int c0 = cg * a.col_width;
-    const int64_t row0 = rg * a.rows_per_cta;
-    int64_t row_end = row0 + a.rows_per_cta;
-    if (row_end > a.n_rows) row_end = a.n_rows;
-    const int n_boxes = row_end > row0 ? (int)((row_end - row0 + a.box_rows - 1) / a.box_rows) : 0;
 
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)a.stages * a.stage_stride);
     uint64_t* empty = full + a.stages;
     __shared__ int s_failed;
+    __shared__ int s_end;          // local box index where this CTA's work ends
+    __shared__ int s_last_fill[8]; // per stage: local index of its last TMA fill, or -1
+    __shared__ int s_fill_open[8]; // per stage: that fill is the stage's latest phase
 
     if (tid == 0) {
         s_failed = 0;
+        s_end = 0x7fffffff;
         for (int s = 0; s < a.stages; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], group_threads);
+            s_last_fill[s] = -1;
+            s_fill_open[s] = 0;
         }
         fence_barrier_init();
     }
@@ -209,34 +236,65 @@ __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_co
 
     if (tid / 32 == producer_warp) {
         // ---------------- producer ----------------
+        // Boxes: a static share first (no atomics on the start-up path),
+        // then chunks from the column group's counter until the work or the
+        // per-CTA cap runs out.  Local box j goes to stage j % stages.
         if (tid % 32 == 0) {
-            int issued = 0;
-            for (int j = 0; j < n_boxes; ++j) {
-                const int s = j % a.stages;
-                const uint32_t use = j / a.stages;
+            int j = 0;
+            bool ok = true;
+            auto stage_free = [&](int jj) -> bool {
+                const int s = jj % a.stages;
+                const uint32_t use = jj / a.stages;
                 if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1)) {
                     atomicOr(a.err, PCAL_DERR_EMPTY_WAIT);
                     s_failed = 1;
-                    break;
+                    return false;
                 }
+                return true;
+            };
+            auto issue = [&](int box) -> bool {
+                if (!stage_free(j)) return false;
+                const int s = j % a.stages;
                 mbar_arrive_expect_tx(&full[s], a.tx_bytes);
-                tma_load_2d(smem + (size_t)s * a.stage_stride, &tmap, c0, (int)(row0 + (int64_t)j * a.box_rows),
-                            &full[s]);
-                issued = j + 1;
+                tma_load_2d(smem + (size_t)s * a.stage_stride, &tmap, c0, box * a.box_rows, &full[s]);
+                s_last_fill[s] = j;
+                s_fill_open[s] = 1;
+                ++j;
+                return true;
+            };
+            for (int b = 0; b < a.static_boxes && ok; ++b) {
+                const int box = (int)rg * a.static_boxes + b;
+                if (box >= a.total_boxes) break;
+                ok = issue(box);
             }
-            // Drain: the most recent fill of every stage must have landed
-            // before the CTA may exit (its shared memory is then reused).
-            for (int s = 0; s < a.stages && s < issued; ++s) {
-                const int last = s + a.stages * ((issued - 1 - s) / a.stages);
-                if (!mbar_wait(&full[s], (uint32_t)(last / a.stages) & 1)) {
-                    atomicOr(a.err, PCAL_DERR_DRAIN_WAIT);
-                    s_failed = 1;
+            // the shared counter was reset by the preceding launch: wait for it
+            grid_dependency_wait();
+            const int base = a.row_groups * a.static_boxes;
+            while (ok && j < a.max_boxes) {
+                const int take = a.chunk < a.max_boxes - j ? a.chunk : a.max_boxes - j;
+                const int v = (int)atomicAdd(&a.sched[cg], (unsigned)take);
+                if (base + v >= a.total_boxes) break;
+                for (int c = 0; c < take && ok && base + v + c < a.total_boxes; ++c) ok = issue(base + v + c);
+            }
+            // end of work: every group gets a data-less phase on the next
+            // stage it owns, after which it reads s_end and stops
+            if (ok) {
+                s_end = j;
+                for (int g = 0; g < a.replicas && ok; ++g) {
+                    int jq = j;
+                    while (jq % a.replicas != g) ++jq;
+                    if (!stage_free(jq)) {
+                        ok = false;
+                        break;
+                    }
+                    s_fill_open[jq % a.stages] = 0;
+                    mbar_arrive(&full[jq % a.stages]);
                 }
             }
         }
     } else {
         // ---------------- consumers ----------------
-        for (int j = q; j < n_boxes; j += a.replicas) {
+        for (int j = q;; j += a.replicas) {
             const int s = j % a.stages;
             const uint32_t use = j / a.stages;
             if (!mbar_wait(&full[s], use & 1)) {
@@ -244,6 +302,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_co
                 s_failed = 1;
                 break;
             }
+            if (j >= *reinterpret_cast<volatile int*>(&s_end)) break;
             const uint32_t* p = reinterpret_cast<const uint32_t*>(smem + (size_t)s * a.stage_stride) + col;
             if (FMT == PCAL_2BIT) {
                 for (int b = 0; b < a.box_rows; b += 32) {
@@ -271,7 +330,19 @@ __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_co
         }
     }
     __syncthreads();
-    if (s_failed) return;
+    allow_dependents();
+    if (s_failed) {
+        // Drain: TMA fills whose phase no consumer waited for must land
+        // before the CTA exits (its shared memory is then reused).
+        if (tid == 0)
+            for (int s = 0; s < a.stages; ++s)
+                if (s_fill_open[s] && s_last_fill[s] >= 0 &&
+                    !mbar_wait(&full[s], (uint32_t)(s_last_fill[s] / a.stages) & 1))
+                    atomicOr(a.err, PCAL_DERR_DRAIN_WAIT);
+        finish_cta(a);
+        return;
+    }
+    grid_dependency_wait();  // the bins were cleared by the preceding finalize
 
     // ---------------- merge replicas, then flush ----------------
     // The stage buffers are free now (every fill landed and was consumed);
@@ -392,6 +463,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_co
             a.partf[rg * a.cols_total + c0 + tid] = make_float2(s, c);
         }
     }
+    finish_cta(a);
 }
 
 // f32: bin k = sum over row groups and over the columns that map to k, in a
@@ -432,6 +504,9 @@ int bits_for(int64_t v) {
     return b;
 }
 
+// Launched as a programmatic dependent of the preceding kernel: its CTAs may
+// start (and stream their static boxes) while that kernel finishes; they wait
+// for it before touching the box counters and the bins.
 template <int FMT, int U>
 cudaError_t launch_one(const CUtensorMap& map, const BulkArgs& a, int grid, int block, size_t smem, cudaStream_t s) {
     auto k = bulk_fold_kernel<FMT, U>;
@@ -441,8 +516,17 @@ cudaError_t launch_one(const CUtensorMap& map, const BulkArgs& a, int grid, int 
         if (e != cudaSuccess) return e;
         smem_set = smem;
     }
-    k<<<grid, block, smem, s>>>(map, a);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, map, a);
 }
 
 }  // namespace
@@ -496,21 +580,30 @@ int bulk_tiling(const pcal_plan* p, int64_t n_rows, BulkTiling* t) {
     z.replicas = r;
     z.stages = stages;
     z.merge_stride = ms;
-    // row groups: one wave over the SMs, rows per CTA a multiple of the box
-    // and small enough for 16-bit per-CTA counts
+    // Work split: boxes of one column group are shared by row_groups CTAs
+    // (one wave over the SMs): a static share each, the rest handed out in
+    // chunks from a counter; each CTA takes at most max_boxes (twice the
+    // average), which keeps its 16-bit per-position counts below 2^16.
+    const int64_t total = (n_rows + box - 1) / box;
+    if (total > 0x3fffffff) return -1;
+    const int64_t cap = 65535 / box;
     int64_t gr = p->num_sms / gc;
     if (gr < 1) gr = 1;
-    int64_t per = (n_rows + gr - 1) / gr;
-    per = (per + box - 1) / box * box;
-    const int64_t max_per = (65535 / box) * box;
-    if (per > max_per) per = max_per;
-    gr = (n_rows + per - 1) / per;
+    if (gr > total) gr = total;
+    while ((total + gr - 1) / gr * 2 > cap) ++gr;  // very long inputs: more CTAs
+    const int64_t avg = (total + gr - 1) / gr;
+    int64_t maxb = 2 * avg;
+    if (maxb > cap) maxb = cap;
+    const int64_t stat = avg * 3 / 4;
     z.row_groups = gr;
-    z.rows_per_cta = per;
+    z.total_boxes = (int)total;
+    z.static_boxes = (int)stat;
+    z.max_boxes = (int)maxb;
+    z.chunk = 2;
+    z.rows_per_cta = maxb * box;  // the most rows one CTA can fold
     z.upper_planes = 0;
     if (p->g.format == PCAL_2BIT) {
-        const int64_t boxes = per / box;
-        const int64_t rows_per_thread = (boxes + r - 1) / r * box;
+        const int64_t rows_per_thread = (maxb + r - 1) / r * box;
         z.upper_planes = bits_for(rows_per_thread / 32);
     }
     z.threads = (wpr * r + 1) * 32;
@@ -559,7 +652,13 @@ cudaError_t launch_bulk(pcal_plan* p, const void* d_rows, int64_t n_rows, int64_
     a.consumers = a.wpr * 32 * t.replicas;
     a.tx_bytes = (uint32_t)((size_t)t.box_rows * t.col_width * 4);
     a.stage_stride = (a.tx_bytes + 1023u) / 1024u * 1024u;
-    a.rows_per_cta = t.rows_per_cta;
+    a.total_boxes = t.total_boxes;
+    a.row_groups = (int)t.row_groups;
+    a.static_boxes = t.static_boxes;
+    a.max_boxes = t.max_boxes;
+    a.chunk = t.chunk;
+    a.sched = p->d_sched;
+    a.done = p->d_sched + kSchedCounters;
     a.n_rows = n_rows;
     a.k_a = k_a;
     a.L = p->g.L;
@@ -627,6 +726,9 @@ extern "C" int pcal_bulk_tiling(double fs, double f_comb, double f_offset, int N
     out->stages = t.stages;
     out->row_groups = t.row_groups;
     out->rows_per_cta = t.rows_per_cta;
+    out->total_boxes = t.total_boxes;
+    out->static_boxes = t.static_boxes;
+    out->max_boxes = t.max_boxes;
     out->upper_planes = t.upper_planes;
     out->threads = t.threads;
     out->smem_bytes = (int64_t)t.smem_bytes;

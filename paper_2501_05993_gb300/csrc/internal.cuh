@@ -28,8 +28,12 @@ struct BulkTiling {
     int replicas;      // consumer threads per column
     int box_rows;      // rows per TMA box (stage)
     int stages;        // pipeline depth
-    int64_t row_groups;      // G_r
-    int64_t rows_per_cta;    // multiple of box_rows
+    int64_t row_groups;      // G_r: CTAs per column group
+    int64_t rows_per_cta;    // the most rows one CTA can fold (max_boxes * box_rows)
+    int total_boxes;         // boxes per column group
+    int static_boxes;        // boxes each CTA takes without the shared counter
+    int max_boxes;           // cap per CTA
+    int chunk;               // boxes per grab from the shared counter
     int upper_planes;  // 2-bit: bit planes above the Harley-Seal tree
     int threads;       // consumer threads + 1 producer warp
     int merge_stride;  // words between rows of the end-of-tile merge area
@@ -45,6 +49,7 @@ struct BulkMapEntry {
     CUtensorMap map;
 };
 constexpr int kBulkMapCache = 16;
+constexpr int kSchedCounters = 8192;  // dynamic box counters (one per column group) + 1
 
 struct pcal_plan {
     pcal_geometry g;
@@ -70,6 +75,7 @@ struct pcal_plan {
     double* d_res;                // results, 5N+3 doubles
     unsigned int* d_ticket;       // [0] fold ticket, [1] dft ticket
     unsigned int* d_err;          // device error flags
+    unsigned int* d_sched;        // bulk kernel box counters [kSchedCounters] + done count
     // host
     double* h_res;                // pinned copy of d_res
     void* h_stage[2];             // pinned staging for pcal_accumulate_host

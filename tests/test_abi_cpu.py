@@ -133,14 +133,17 @@ def test_bulk_tiling_invariants(lib, fs, fc, fo, fmt, num_sms, n_rows):
     assert 1 <= t.box_rows <= 256
     if fmt == pcal.PCAL_2BIT:
         assert t.box_rows % 32 == 0                                  # whole add32 blocks
-        rows_per_thread = -(-(t.rows_per_cta // t.box_rows) // t.replicas) * t.box_rows
+        rows_per_thread = -(-t.max_boxes // t.replicas) * t.box_rows
         assert rows_per_thread // 32 < (1 << t.upper_planes) or t.upper_planes == 0 and rows_per_thread < 32
         assert t.upper_planes <= 11
         ms = (t.col_width + 31) // 32 * 32 + 2
         assert t.replicas * t.col_width * 128 + 128 * ms <= t.stages * ((t.box_rows * t.col_width * 4 + 1023) // 1024 * 1024)
     assert t.stages % t.replicas == 0 and t.stages >= 3             # one consumer group per stage
-    assert t.rows_per_cta % t.box_rows == 0 and t.rows_per_cta <= 65535
-    assert t.row_groups * t.rows_per_cta >= n_rows > (t.row_groups - 1) * t.rows_per_cta
+    assert t.rows_per_cta == t.max_boxes * t.box_rows <= 65535       # 16-bit per-CTA counts
+    assert t.total_boxes == -(-n_rows // t.box_rows)
+    # every box is taken: static shares, then the counter, within the caps
+    assert t.row_groups * t.max_boxes >= t.total_boxes
+    assert t.static_boxes <= t.max_boxes and t.row_groups * t.static_boxes <= t.total_boxes
     wpr = (t.col_width + 31) // 32
     assert t.threads == (wpr * t.replicas + 1) * 32 <= 640
     assert t.smem_bytes + 1024 <= 227 * 1024
