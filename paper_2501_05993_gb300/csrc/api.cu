@@ -190,6 +190,7 @@ extern "C" int pcal_accumulate(pcal_plan* p, const void* samples, int64_t n, voi
                 cudaError_t e = launch_spill2(p, s);
                 if (e != cudaSuccess) return cuda_status(e);
                 p->since_spill = 0;
+                p->spilled = true;
             }
         }
         int rc = accumulate_run(p, d, take, s);
@@ -256,6 +257,7 @@ extern "C" int pcal_finalize_device(pcal_plan* p, void* stream) {
     p->last_stream = s;
     p->period_start = p->n_abs;
     p->since_spill = 0;
+    p->spilled = false;
     p->results_valid = true;
     return PCAL_OK;
 }

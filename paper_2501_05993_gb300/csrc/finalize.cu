@@ -37,6 +37,7 @@ constexpr int kDftTonesPerCta = 32;
 
 struct FinArgs {
     int fmt;
+    int spilled;  // 2-bit: the wide arrays hold counts of this period
     int bc;   // residues b per fold CTA
     int tpb;  // threads per residue (power of two)
     int64_t L, N, so;
@@ -57,18 +58,15 @@ struct FinArgs {
     unsigned int* ticket;
 };
 
-// Decode bin k to its real value S[k] (FP64) and clear it for the next period.
-__device__ __forceinline__ double take_bin(const FinArgs& a, int64_t k) {
+// Decode bin k to its real value S[k] (FP64).
+__device__ __forceinline__ double read_bin(const FinArgs& a, int64_t k) {
     if (a.fmt == PCAL_2BIT) {
         const unsigned long long v = a.acc2[k];
-        const unsigned long long sl = (v & PCAL_F21_MASK) + a.wide2[k];
-        const unsigned long long sh = ((v >> 21) & PCAL_F21_MASK) + a.wide2[a.L + k];
-        const unsigned long long shl = ((v >> 42) & PCAL_F21_MASK) + a.wide2[2 * a.L + k];
-        if (v) a.acc2[k] = 0;
-        if (sl | sh) {
-            a.wide2[k] = 0;
-            a.wide2[a.L + k] = 0;
-            a.wide2[2 * a.L + k] = 0;
+        unsigned long long sl = v & PCAL_F21_MASK, sh = (v >> 21) & PCAL_F21_MASK, shl = (v >> 42) & PCAL_F21_MASK;
+        if (a.spilled) {
+            sl += a.wide2[k];
+            sh += a.wide2[a.L + k];
+            shl += a.wide2[2 * a.L + k];
         }
         int64_t r = k - a.a0;
         if (r < 0) r += a.L;
@@ -77,14 +75,25 @@ __device__ __forceinline__ double take_bin(const FinArgs& a, int64_t k) {
         // count[1] = sl - shl, count[0] = cnt - sl - sh + shl.
         return a.lev0 * cnt + a.c_l * (double)sl + a.c_h * (double)sh + a.c_hl * (double)shl;
     }
-    if (a.fmt == PCAL_I8) {
-        const long long v = a.acc8[k];
-        if (v) a.acc8[k] = 0;
-        return (double)v;
-    }
+    if (a.fmt == PCAL_I8) return (double)a.acc8[k];
     const float2 v = a.accf[k];
-    a.accf[k] = make_float2(0.f, 0.f);
     return (double)v.x + (double)v.y;
+}
+
+// Clear bin k for the next integration period.
+__device__ __forceinline__ void clear_bin(const FinArgs& a, int64_t k) {
+    if (a.fmt == PCAL_2BIT) {
+        a.acc2[k] = 0;
+        if (a.spilled) {
+            a.wide2[k] = 0;
+            a.wide2[a.L + k] = 0;
+            a.wide2[2 * a.L + k] = 0;
+        }
+    } else if (a.fmt == PCAL_I8) {
+        a.acc8[k] = 0;
+    } else {
+        a.accf[k] = make_float2(0.f, 0.f);
+    }
 }
 
 // Programmatic dependent launch: wait for the preceding kernel's results;
@@ -327,7 +336,7 @@ __global__ void fin_fold_kernel(FinArgs a) {
     if (active) {
         for (int64_t m = sub; m < per; m += tpb) {
             const int64_t k = b + m * a.N;
-            const double S = take_bin(a, k);
+            const double S = read_bin(a, k);
             const double2 w = a.tw[(a.so * k) % a.L];
             re = fma(S, w.x, re);
             im = fma(S, w.y, im);
@@ -359,6 +368,10 @@ __global__ void fin_fold_kernel(FinArgs a) {
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) is_last = atomicAdd(&a.ticket[0], 1u) == gridDim.x - 1;
+    // clear this CTA's bins for the next period; the fence above did not
+    // have to wait for these stores
+    if (active)
+        for (int64_t m = sub; m < per; m += tpb) clear_bin(a, b + m * a.N);
     __syncthreads();
     if (!is_last) return;
     __threadfence();
@@ -435,6 +448,7 @@ cudaError_t launch_finalize(pcal_plan* p, cudaStream_t s) {
     FinArgs a{};
     const pcal_geometry& g = p->g;
     a.fmt = g.format;
+    a.spilled = p->spilled ? 1 : 0;
     a.L = g.L;
     a.N = g.N;
     a.so = g.step_offset;

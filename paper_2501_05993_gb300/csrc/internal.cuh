@@ -61,6 +61,7 @@ struct pcal_plan {
     int64_t n_abs;        // samples accumulated since creation
     int64_t period_start; // absolute index of the first sample of this period
     int64_t since_spill;  // 2-bit: samples added since the last spill
+    bool spilled;         // 2-bit: the wide arrays hold counts of this period
     // device state
     unsigned long long* d_acc2;   // 2-bit packed counts [L]
     unsigned long long* d_wide2;  // 2-bit spilled counts [3][L]
