@@ -216,6 +216,36 @@ typedef struct {
 int pcal_bulk_tiling(double fs, double f_comb, double f_offset, int N, int sample_format, int num_sms,
                      int64_t n_rows, pcal_tiling* out);
 
+/*
+ * pcal_tones_from_counts_noalloc -- the finalize (decode, rotate, fold to N,
+ * DFT, products) for callers that cannot allocate GPU memory: code that runs
+ * inside a fixed memory pool or arena, a process whose device memory is
+ * budgeted up front, or a stream being captured into a CUDA graph (where a
+ * cudaMalloc is not allowed).  It creates no plan and calls no cudaMalloc,
+ * cudaFree or allocating library routine.  The paper has no counterpart:
+ * this is an interface choice of this library.
+ *   fs, f_comb, f_offset, N: validated as in pcal_plan_geometry; N must be
+ *            at most 1024 (PCAL_ETOOLARGE otherwise).
+ *   d_counts: DEVICE, int64 [L][4], the per-(bin, code) counts of a 2-bit
+ *            stream as pcal_get_bins returns them (bin k = samples with
+ *            absolute index n = k mod L).  Read only.
+ *   n_samples: samples the counts cover (the M of the amplitude 2|T|/M).
+ *   levels:  HOST, the 4 code values.
+ *   d_results: DEVICE, 5N+3 doubles, written with the layout of
+ *            pcal_result_device.
+ *   stream:  cudaStream_t; the call only enqueues work.
+ * Scratch lives in a static device array of about 24.6 KB that every GPU
+ * loading the library holds until the process exits.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) with
+ * the device current; make that first call before any stream capture.  All
+ * calls on a device share the array and it keeps the previous call's
+ * contents (the call clears what must start at zero), so calls whose GPU
+ * work overlaps -- on different streams or host threads -- race; serialise
+ * them.
+ */
+int pcal_tones_from_counts_noalloc(double fs, double f_comb, double f_offset, int N, const int64_t* d_counts,
+                                   int64_t n_samples, const double levels[4], double* d_results, void* stream);
+
 /* Static name of a status code. */
 const char* pcal_strerror(int code);
 

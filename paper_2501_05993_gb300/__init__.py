@@ -91,6 +91,7 @@ def load(path: str | None = None):
         "pcal_get_stats": ([vp, P(Stats)], ci),
         "pcal_strerror": ([ci], ctypes.c_char_p),
         "pcal_bulk_tiling": ([dbl, dbl, dbl, ci, ci, ci, i64, P(Tiling)], ci),
+        "pcal_tones_from_counts_noalloc": ([dbl, dbl, dbl, ci, vp, i64, P(dbl), vp, vp], ci),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -208,6 +209,16 @@ def pcal_bulk_tiling(fs, f_comb, f_offset, N, sample_format, num_sms, n_rows) ->
     _check(load().pcal_bulk_tiling(float(fs), float(f_comb), float(f_offset), int(N), int(sample_format),
                                    int(num_sms), int(n_rows), ctypes.byref(t)), "pcal_bulk_tiling")
     return t
+
+
+def pcal_tones_from_counts_noalloc(fs, f_comb, f_offset, N, d_counts, n_samples, levels, d_results,
+                                   stream=None) -> None:
+    """Finalize from device counts [L][4] into a device result buffer of
+    5N+3 doubles, without any allocation (see include/pcal.h)."""
+    lv = (ctypes.c_double * 4)(*[float(v) for v in levels])
+    _check(load().pcal_tones_from_counts_noalloc(float(fs), float(f_comb), float(f_offset), int(N), _ptr(d_counts),
+                                                 int(n_samples), lv, _ptr(d_results), _stream(stream)),
+           "pcal_tones_from_counts_noalloc")
 
 
 def pcal_get_stats(plan: int) -> Stats:

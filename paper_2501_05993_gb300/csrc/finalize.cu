@@ -25,6 +25,8 @@
 // kernel spreads the DFT over CTAs and its last CTA runs the products.
 #include <math.h>
 
+#include <mutex>
+
 #include "df64.cuh"
 #include "internal.cuh"
 
@@ -50,6 +52,8 @@ struct FinArgs {
     unsigned long long* wide2;
     long long* acc8;
     float2* accf;  // float32 bins in df (hi, lo)
+    const long long* counts4;  // no-allocation entry: the caller's counts [L][4]
+    double lev[4];             // no-allocation entry: the code levels
     const double2* tw;
     const float2* twN;
     float4* P;     // P[b] as df re (x, y), df im (z, w)
@@ -58,8 +62,14 @@ struct FinArgs {
     unsigned int* ticket;
 };
 
-// Decode bin k to its real value S[k] (FP64).
+// Decode bin k to its real value S[k] (FP64).  NoAlloc: the caller's
+// per-(bin, code) counts.
+template <bool NoAlloc>
 __device__ __forceinline__ double read_bin(const FinArgs& a, int64_t k) {
+    if constexpr (NoAlloc) {
+        const long long* c = a.counts4 + 4 * k;
+        return a.lev[0] * (double)c[0] + a.lev[1] * (double)c[1] + a.lev[2] * (double)c[2] + a.lev[3] * (double)c[3];
+    }
     if (a.fmt == PCAL_2BIT) {
         const unsigned long long v = a.acc2[k];
         unsigned long long sl = v & PCAL_F21_MASK, sh = (v >> 21) & PCAL_F21_MASK, shl = (v >> 42) & PCAL_F21_MASK;
@@ -78,6 +88,17 @@ __device__ __forceinline__ double read_bin(const FinArgs& a, int64_t k) {
     if (a.fmt == PCAL_I8) return (double)a.acc8[k];
     const float2 v = a.accf[k];
     return (double)v.x + (double)v.y;
+}
+
+// exp(-j*2*pi*m/L): the plan's table; NoAlloc evaluates it here.
+template <bool NoAlloc>
+__device__ __forceinline__ double2 rotator(const FinArgs& a, int64_t m) {
+    if constexpr (NoAlloc) {
+        double sn, cs;
+        sincospi(2.0 * (double)m / (double)a.L, &sn, &cs);
+        return make_double2(cs, -sn);
+    }
+    return a.tw[m];
 }
 
 // Clear bin k for the next integration period.
@@ -159,12 +180,19 @@ __device__ __forceinline__ float wrap_pi_f(float x) {
 // when sT is given, to shared memory.  P (hi + lo) and the twiddles are
 // staged in shared memory first.  Groups of g threads (a power of two <= 32)
 // share a tone and combine their partial sums with a fixed butterfly.
+template <bool NoAlloc>
 __device__ void dft_tones(const FinArgs& a, int64_t i0, int64_t i1, float2* sP, float2* sTw, float2* sT) {
     const int64_t N = a.N;
     for (int64_t b = threadIdx.x; b < N; b += blockDim.x) {
         const float4 v = __ldcg(&a.P[b]);
         sP[b] = make_float2(v.x + v.y, v.z + v.w);
-        sTw[b] = a.twN[b];
+        if constexpr (NoAlloc) {
+            float sn, cs;
+            sincospif(2.0f * (float)b / (float)N, &sn, &cs);
+            sTw[b] = make_float2(cs, -sn);
+        } else {
+            sTw[b] = a.twN[b];
+        }
     }
     __syncthreads();
     const int64_t ntone = i1 - i0;
@@ -322,6 +350,7 @@ __device__ void tone_products(const FinArgs& a, const ProductsSmem& m) {
 // Thread t works on residue b = blockIdx.x*bc + t/tpb and bins b + m*N for
 // m = t%tpb, t%tpb + tpb, ...; the tpb threads of a residue are contiguous
 // (tpb a power of two) and combine with shuffles, then across warps.
+template <bool NoAlloc>
 __global__ void fin_fold_kernel(FinArgs a) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ bool is_last;
@@ -336,8 +365,8 @@ __global__ void fin_fold_kernel(FinArgs a) {
     if (active) {
         for (int64_t m = sub; m < per; m += tpb) {
             const int64_t k = b + m * a.N;
-            const double S = read_bin(a, k);
-            const double2 w = a.tw[(a.so * k) % a.L];
+            const double S = read_bin<NoAlloc>(a, k);
+            const double2 w = rotator<NoAlloc>(a, (a.so * k) % a.L);
             re = fma(S, w.x, re);
             im = fma(S, w.y, im);
         }
@@ -370,7 +399,7 @@ __global__ void fin_fold_kernel(FinArgs a) {
     if (threadIdx.x == 0) is_last = atomicAdd(&a.ticket[0], 1u) == gridDim.x - 1;
     // clear this CTA's bins for the next period; the fence above did not
     // have to wait for these stores
-    if (active)
+    if (!NoAlloc && active)
         for (int64_t m = sub; m < per; m += tpb) clear_bin(a, b + m * a.N);
     __syncthreads();
     if (!is_last) return;
@@ -380,12 +409,13 @@ __global__ void fin_fold_kernel(FinArgs a) {
         // shared memory: products area, then P and the twiddles for the DFT
         const ProductsSmem m = products_layout(smem, a.N);
         float2* sP = reinterpret_cast<float2*>(smem + products_bytes(a.N));
-        dft_tones(a, 0, a.N, sP, sP + a.N, m.T);
+        dft_tones<NoAlloc>(a, 0, a.N, sP, sP + a.N, m.T);
         tone_products(a, m);
     }
 }
 
 // Spread DFT for large N; the last CTA runs the products.
+template <bool NoAlloc>
 __global__ void fin_dft_kernel(FinArgs a) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ bool is_last;
@@ -394,7 +424,7 @@ __global__ void fin_dft_kernel(FinArgs a) {
     const int64_t i0 = (int64_t)blockIdx.x * kDftTonesPerCta;
     const int64_t i1 = i0 + kDftTonesPerCta < a.N ? i0 + kDftTonesPerCta : a.N;
     float2* sP = reinterpret_cast<float2*>(smem);
-    dft_tones(a, i0, i1, sP, sP + a.N, nullptr);
+    dft_tones<NoAlloc>(a, i0, i1, sP, sP + a.N, nullptr);
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) is_last = atomicAdd(&a.ticket[1], 1u) == gridDim.x - 1;
@@ -444,15 +474,69 @@ cudaError_t launch_init_twiddles(pcal_plan* p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(pcal_plan* p, cudaStream_t s) {
-    FinArgs a{};
-    const pcal_geometry& g = p->g;
-    a.fmt = g.format;
-    a.spilled = p->spilled ? 1 : 0;
+namespace {
+
+// Launch the finalize kernels for filled-in arguments (everything but the
+// work split, which is chosen here).
+template <bool NoAlloc>
+cudaError_t launch_finalize_args(FinArgs a, int num_sms, cudaStream_t s, int* launches) {
+    const int64_t N = a.N;
+    int G = (int)(N < num_sms ? N : num_sms);
+    a.bc = (int)((N + G - 1) / G);
+    G = (int)((N + a.bc - 1) / a.bc);
+    // tpb = the largest power of two with bc*tpb <= 256; the block is a
+    // multiple of 32 threads (the shuffles and the DFT need whole warps)
+    a.tpb = 1;
+    while (a.bc * a.tpb * 2 <= 256) a.tpb *= 2;
+    const int threads = (a.bc * a.tpb + 31) / 32 * 32;
+    size_t smem = (size_t)threads * 16;
+    if (N <= kDftInFoldMaxN) {
+        const size_t need = products_bytes(N) + (size_t)N * 16;  // products + P + twiddles
+        if (need > smem) smem = need;
+    }
+    cudaError_t e = cudaSuccess;
+    static size_t fold_smem_set = 0;
+    if (smem > 48 * 1024 && smem > fold_smem_set) {
+        e = cudaFuncSetAttribute(fin_fold_kernel<NoAlloc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        fold_smem_set = smem;
+    }
+    e = launch_pdl(fin_fold_kernel<NoAlloc>, G, threads, smem, s, a);
+    *launches += 1;
+    if (e != cudaSuccess || N <= kDftInFoldMaxN) return e;
+    const int threads2 = 256;
+    const size_t smem2 = (size_t)N * 16 > products_bytes(N) ? (size_t)N * 16 : products_bytes(N);
+    static size_t dft_smem_set = 0;
+    if (smem2 > 48 * 1024 && smem2 > dft_smem_set) {
+        e = cudaFuncSetAttribute(fin_dft_kernel<NoAlloc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+        if (e != cudaSuccess) return e;
+        dft_smem_set = smem2;
+    }
+    e = launch_pdl(fin_dft_kernel<NoAlloc>, (int)((N + kDftTonesPerCta - 1) / kDftTonesPerCta), threads2, smem2, s, a);
+    *launches += 1;
+    return e;
+}
+
+void set_common(FinArgs& a, const pcal_geometry& g, int64_t n_tot) {
     a.L = g.L;
     a.N = g.N;
     a.so = g.step_offset;
+    a.M = (double)n_tot;
+    a.two_over_m = n_tot > 0 ? (float)(2.0 / (double)n_tot) : 0.0f;
+    const double tpf = 6.283185307179586476925 * (double)g.f_comb;
+    a.two_pi_fc.hi = (float)tpf;
+    a.two_pi_fc.lo = (float)(tpf - (double)a.two_pi_fc.hi);
+}
+
+}  // namespace
+
+cudaError_t launch_finalize(pcal_plan* p, cudaStream_t s) {
+    FinArgs a{};
+    const pcal_geometry& g = p->g;
     const int64_t n_tot = p->n_abs - p->period_start;
+    set_common(a, g, n_tot);
+    a.fmt = g.format;
+    a.spilled = p->spilled ? 1 : 0;
     a.q = n_tot / g.L;
     a.rem = n_tot % g.L;
     a.a0 = p->period_start % g.L;
@@ -461,11 +545,6 @@ cudaError_t launch_finalize(pcal_plan* p, cudaStream_t s) {
     a.c_l = lv[1] - lv[0];
     a.c_h = lv[2] - lv[0];
     a.c_hl = lv[3] - lv[2] - lv[1] + lv[0];
-    a.M = (double)n_tot;
-    a.two_over_m = n_tot > 0 ? (float)(2.0 / (double)n_tot) : 0.0f;
-    const double tpf = 6.283185307179586476925 * (double)g.f_comb;
-    a.two_pi_fc.hi = (float)tpf;
-    a.two_pi_fc.lo = (float)(tpf - (double)a.two_pi_fc.hi);
     a.acc2 = p->d_acc2;
     a.wide2 = p->d_wide2;
     a.acc8 = p->d_acc8;
@@ -476,39 +555,97 @@ cudaError_t launch_finalize(pcal_plan* p, cudaStream_t s) {
     a.T = reinterpret_cast<float2*>(p->d_T);
     a.res = p->d_res;
     a.ticket = p->d_ticket;
-
-    int G = (int)(g.N < p->num_sms ? g.N : p->num_sms);
-    a.bc = (int)((g.N + G - 1) / G);
-    G = (int)((g.N + a.bc - 1) / a.bc);
-    // tpb = the largest power of two with bc*tpb <= 256; the block is a
-    // multiple of 32 threads (the shuffles and the DFT need whole warps)
-    a.tpb = 1;
-    while (a.bc * a.tpb * 2 <= 256) a.tpb *= 2;
-    const int threads = (a.bc * a.tpb + 31) / 32 * 32;
-    size_t smem = (size_t)threads * 16;
-    if (g.N <= kDftInFoldMaxN) {
-        const size_t need = products_bytes(g.N) + (size_t)g.N * 16;  // products + P + twiddles
-        if (need > smem) smem = need;
-    }
-    cudaError_t e = cudaSuccess;
-    static size_t fold_smem_set = 0;
-    if (smem > 48 * 1024 && smem > fold_smem_set) {
-        e = cudaFuncSetAttribute(fin_fold_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        fold_smem_set = smem;
-    }
-    e = launch_pdl(fin_fold_kernel, G, threads, smem, s, a);
-    p->stats.kernel_launches += 1;
-    if (e != cudaSuccess || g.N <= kDftInFoldMaxN) return e;
-    const int threads2 = 256;
-    const size_t smem2 = (size_t)g.N * 16 > products_bytes(g.N) ? (size_t)g.N * 16 : products_bytes(g.N);
-    static size_t dft_smem_set = 0;
-    if (smem2 > 48 * 1024 && smem2 > dft_smem_set) {
-        e = cudaFuncSetAttribute(fin_dft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
-        if (e != cudaSuccess) return e;
-        dft_smem_set = smem2;
-    }
-    e = launch_pdl(fin_dft_kernel, (int)((g.N + kDftTonesPerCta - 1) / kDftTonesPerCta), threads2, smem2, s, a);
-    p->stats.kernel_launches += 1;
+    int launches = 0;
+    cudaError_t e = launch_finalize_args<false>(a, p->num_sms, s, &launches);
+    p->stats.kernel_launches += launches;
     return e;
+}
+
+// ---- finalize without any allocation -------------------------------------------
+//
+// Some callers cannot allocate GPU memory at all: code running inside a
+// pre-sized memory pool or arena, a process whose device memory budget is
+// fixed at start-up, or a stream that is being captured into a CUDA graph,
+// where a cudaMalloc is not allowed.  For them pcal_tones_from_counts_noalloc
+// runs the finalize kernels with their scratch (the folded bins P, the tone
+// phasors T and the completion tickets) in the file-scope array below, which
+// every GPU that loads this library holds until the process exits; the
+// rotator and DFT twiddles are evaluated on the fly instead of read from a
+// plan's tables.  Everything else comes from the caller.
+
+namespace {
+
+constexpr int kNoAllocMaxN = 1024;
+
+struct NoAllocScratch {
+    float4 P[kNoAllocMaxN];
+    float2 T[kNoAllocMaxN];
+    unsigned int ticket[4];
+};
+
+// ~24.6 KB per device.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+NoAllocScratch* g_noalloc_ptr[kMaxDevices];  // device address of the array, per device
+int g_noalloc_sms[kMaxDevices];
+
+// Device address of the scratch array on the current device.  In host code
+// the array's name is only a host-side stand-in, so the address must come
+// from cudaGetSymbolAddress, once per device, with that device current.
+cudaError_t noalloc_scratch(NoAllocScratch** out, int* num_sms) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&g_noalloc_sms[dev], cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = static_cast<NoAllocScratch*>(ptr);
+    }
+    *out = g_noalloc_ptr[dev];
+    *num_sms = g_noalloc_sms[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" int pcal_tones_from_counts_noalloc(double fs, double f_comb, double f_offset, int N,
+                                              const int64_t* d_counts, int64_t n_samples, const double levels[4],
+                                              double* d_results, void* stream) {
+    pcal_geometry g;
+    int rc = pcal_plan_geometry(fs, f_comb, f_offset, N, PCAL_2BIT, &g);
+    if (rc != PCAL_OK) return rc;
+    if (g.N > kNoAllocMaxN) return PCAL_ETOOLARGE;
+    if (!d_counts || !d_results || !levels || n_samples < 0) return PCAL_EINVAL;
+    for (int i = 0; i < 4; ++i)
+        if (!(levels[i] == levels[i]) || levels[i] > 1e300 || levels[i] < -1e300) return PCAL_EINVAL;
+    NoAllocScratch* sc = nullptr;
+    int num_sms = 0;
+    cudaError_t e = noalloc_scratch(&sc, &num_sms);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? PCAL_ENOMEM : PCAL_ECUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // the completion tickets must start at zero (the array keeps whatever the
+    // previous call, possibly an interrupted one, left there)
+    e = cudaMemsetAsync(sc->ticket, 0, sizeof(sc->ticket), s);
+    if (e != cudaSuccess) return PCAL_ECUDA;
+    FinArgs a{};
+    set_common(a, g, n_samples);
+    a.fmt = PCAL_2BIT;
+    a.counts4 = reinterpret_cast<const long long*>(d_counts);
+    for (int i = 0; i < 4; ++i) a.lev[i] = levels[i];
+    a.tw = nullptr;   // rotator evaluated per bin (no plan table)
+    a.twN = nullptr;  // DFT twiddles evaluated per CTA
+    a.P = sc->P;
+    a.T = sc->T;
+    a.ticket = sc->ticket;
+    a.res = d_results;
+    int launches = 0;
+    e = launch_finalize_args<true>(a, num_sms, s, &launches);
+    return e == cudaSuccess ? PCAL_OK : PCAL_ECUDA;
 }
