@@ -122,6 +122,14 @@ __device__ __forceinline__ void clear_bin(const FinArgs& a, int64_t k) {
 __device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
+// Completion ticket: a release-acquire increment, so the arriving CTA's
+// stores are visible to the CTA that draws the last ticket.
+__device__ __forceinline__ unsigned int ticket_acq_rel(unsigned int* t) {
+    unsigned int old;
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(t) : "memory");
+    return old;
+}
+
 __device__ __forceinline__ df df_of(double x) {
     const float hi = (float)x;
     return df{hi, (float)(x - (double)hi)};
@@ -131,17 +139,21 @@ __device__ __forceinline__ df shfl_xor_df(df v, int o) {
     return df{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
 }
 
-// K block-wide df sums (fixed order: warp butterflies, then warp totals in
-// warp order); every thread receives them.  blockDim.x: a multiple of 32;
-// sm: 32*K float2.
+// K block-wide df sums (fixed order: warp butterflies, then the totals of
+// the first nw warps in warp order -- the other warps hold zeros); every
+// thread receives them.  blockDim.x: a multiple of 32; sm: 32*K float2.
 template <int K>
-__device__ void block_sums_df(df (&v)[K], float2* sm) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+__device__ void block_sums_df(df (&v)[K], float2* sm, int nw) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int j = 0; j < K; ++j)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v[j] = pcal_df::add(v[j], shfl_xor_df(v[j], o));
-    if (lane == 0)
+    if (nw == 1) {
+        __syncthreads();  // keep the barrier count equal for every nw
+        return;
+    }
+    if (lane == 0 && warp < nw)
 #pragma unroll
         for (int j = 0; j < K; ++j) sm[warp * K + j] = make_float2(v[j].hi, v[j].lo);
     __syncthreads();
@@ -261,6 +273,7 @@ __device__ void tone_products(const FinArgs& a, const ProductsSmem& m) {
     const int t = threadIdx.x;
     int nt = (int)((N + 7) / 8 + 31) / 32 * 32;
     if (nt > (int)blockDim.x) nt = blockDim.x;
+    const int nw = nt / 32;  // warps holding tones
     const int64_t chunk = (N + nt - 1) / nt;
     const int64_t c0 = t < nt ? (t * chunk < N ? t * chunk : N) : N;
     const int64_t c1 = c0 + chunk < N ? c0 + chunk : N;
@@ -289,12 +302,13 @@ __device__ void tone_products(const FinArgs& a, const ProductsSmem& m) {
         s3[1] = pcal_df::add(s3[1], pcal_df::two_prod(w, (float)i));
         s3[2] = pcal_df::add(s3[2], pcal_df::mul_f(df{m.un[i].x, m.un[i].y}, w));
     }
-    block_sums_df<3>(s3, m.red);
+    block_sums_df<3>(s3, m.red, nw);
     const df W = s3[0];
     df td{__int_as_float(0x7fc00000), 0.f}, sig{__int_as_float(0x7fc00000), 0.f};  // NaN until fitted
     if (N >= 2 && W.hi > 0.f) {
         const df xbar = pcal_df::div(s3[1], W), ubar = pcal_df::div(s3[2], W);
-        df s2[2] = {{0.f, 0.f}, {0.f, 0.f}};
+        // centred sums; the residual sum follows from Syy - slope*Sxu
+        df s2[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         for (int64_t i = c0; i < c1; ++i) {
             const float2 z = m.T[i];
             const float w = z.x * z.x + z.y * z.y;
@@ -303,23 +317,18 @@ __device__ void tone_products(const FinArgs& a, const ProductsSmem& m) {
             const df wdx = pcal_df::mul_f(dx, w);
             s2[0] = pcal_df::add(s2[0], pcal_df::mul(wdx, dx));
             s2[1] = pcal_df::add(s2[1], pcal_df::mul(wdx, du));
+            s2[2] = pcal_df::add(s2[2], pcal_df::mul_f(pcal_df::mul(du, du), w));
         }
-        block_sums_df<2>(s2, m.red);
+        block_sums_df<3>(s2, m.red, nw);
         if (s2[0].hi > 0.f) {
             const df slope = pcal_df::div(s2[1], s2[0]);  // rad per tone index
-            df s1[1] = {{0.f, 0.f}};
-            for (int64_t i = c0; i < c1; ++i) {
-                const float2 z = m.T[i];
-                const float w = z.x * z.x + z.y * z.y;
-                const df dx = pcal_df::sub(df{(float)i, 0.f}, xbar);
-                const df r = pcal_df::sub(pcal_df::sub(df{m.un[i].x, m.un[i].y}, ubar), pcal_df::mul(slope, dx));
-                s1[0] = pcal_df::add(s1[0], pcal_df::mul_f(pcal_df::mul(r, r), w));
-            }
-            block_sums_df<1>(s1, m.red);
             td = pcal_df::div(slope, a.two_pi_fc);
-            if (N > 2)
-                sig = pcal_df::div(pcal_df::sqrt_df(pcal_df::div(pcal_df::div(s1[0], df{(float)(N - 2), 0.f}), s2[0])),
+            if (N > 2) {
+                df ssr = pcal_df::sub(s2[2], pcal_df::mul(slope, s2[1]));
+                if (ssr.hi < 0.f) ssr = df{0.f, 0.f};
+                sig = pcal_df::div(pcal_df::sqrt_df(pcal_df::div(ssr, pcal_df::mul_f(s2[0], (float)(N - 2)))),
                                    a.two_pi_fc);
+            }
         }
     }
     if (t == 0) {
@@ -394,9 +403,9 @@ __global__ void fin_fold_kernel(FinArgs a) {
             a.P[b] = make_float4(sr.hi, sr.lo, si.hi, si.lo);
         }
     }
-    __threadfence();
+    __threadfence();  // the P stores of this CTA's writers
     __syncthreads();
-    if (threadIdx.x == 0) is_last = atomicAdd(&a.ticket[0], 1u) == gridDim.x - 1;
+    if (threadIdx.x == 0) is_last = ticket_acq_rel(&a.ticket[0]) == gridDim.x - 1;
     // clear this CTA's bins for the next period; the fence above did not
     // have to wait for these stores
     if (!NoAlloc && active)
@@ -425,9 +434,9 @@ __global__ void fin_dft_kernel(FinArgs a) {
     const int64_t i1 = i0 + kDftTonesPerCta < a.N ? i0 + kDftTonesPerCta : a.N;
     float2* sP = reinterpret_cast<float2*>(smem);
     dft_tones<NoAlloc>(a, i0, i1, sP, sP + a.N, nullptr);
-    __threadfence();
+    __threadfence();  // the T stores of this CTA
     __syncthreads();
-    if (threadIdx.x == 0) is_last = atomicAdd(&a.ticket[1], 1u) == gridDim.x - 1;
+    if (threadIdx.x == 0) is_last = ticket_acq_rel(&a.ticket[1]) == gridDim.x - 1;
     __syncthreads();
     if (!is_last) return;
     __threadfence();

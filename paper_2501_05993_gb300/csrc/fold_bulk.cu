@@ -366,46 +366,59 @@ __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_co
             if (5 + u < 16) W[5 + u] = acc2.wu[u];
             if (4 + u < 16) D[4 + u] = acc2.du[u];
         }
-        // replicas add up pairwise in the bit-plane domain (ripple-carry adds
-        // of 16-plane numbers; per-CTA counts stay below 2^16).
-        // scratch[(i*r + q)*C_w + col], i < 32 (16 w planes, 16 d planes)
+        // Replicas add up in the bit-plane domain (ripple-carry adds of
+        // 16-plane numbers; per-CTA counts stay below 2^16): group 0 gathers
+        // the l/h planes W, group 1 the (h AND l) planes D, and each of the two
+        // transposes its planes into counts, so the work splits in half.
+        // scratch[(i*r + q)*C_w + col], i < 32 (16 W planes, 16 D planes)
         uint32_t* scratch = reinterpret_cast<uint32_t*>(smem);
         const int rc = a.replicas * a.col_width;
-        for (int step = 1; step < a.replicas; step <<= 1) {
-            if (active && q % (2 * step) == step) {
-                uint32_t* dst = scratch + q * a.col_width + col;
+        const int qd = a.replicas > 1 ? 1 : 0;  // the group that gathers D
+        if (active) {
+            uint32_t* dst = scratch + q * a.col_width + col;
+            if (q != 0)
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    dst[i * rc] = W[i];
-                    dst[(16 + i) * rc] = D[i];
-                }
-            }
-            __syncthreads();
-            if (active && q % (2 * step) == 0 && q + step < a.replicas) {
-                const uint32_t* src = scratch + (q + step) * a.col_width + col;
-                uint32_t cw = 0, cd = 0;
+                for (int i = 0; i < 16; ++i) dst[i * rc] = W[i];
+            if (q != qd)
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const uint32_t bw = src[i * rc], bd = src[(16 + i) * rc];
-                    const uint32_t sw = pcal_bits::lop3<pcal_bits::kXor3>(W[i], bw, cw);
-                    cw = pcal_bits::lop3<pcal_bits::kMaj3>(W[i], bw, cw);
-                    W[i] = sw;
-                    const uint32_t sd = pcal_bits::lop3<pcal_bits::kXor3>(D[i], bd, cd);
-                    cd = pcal_bits::lop3<pcal_bits::kMaj3>(D[i], bd, cd);
-                    D[i] = sd;
-                }
-            }
-            __syncthreads();
+                for (int i = 0; i < 16; ++i) dst[(16 + i) * rc] = D[i];
         }
-        // counts of column col: m[i*S + col], i < 32, S = a.merge_stride
-        uint32_t* m = scratch + 32 * rc;
-        if (active && q == 0) {
-            pcal_bits::transpose16x2(W);
-            pcal_bits::transpose16x2(D);
+        __syncthreads();
+        uint32_t* m = scratch + 32 * rc;  // counts of column col: m[i*S + col], i < 32
+        if (active && (q == 0 || q == qd)) {
+            for (int o = 0; o < a.replicas; ++o) {
+                if (o == q) continue;
+                const uint32_t* src = scratch + o * a.col_width + col;
+                if (q == 0) {
+                    uint32_t c = 0;
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                m[i * a.merge_stride + col] = W[i];
-                m[(16 + i) * a.merge_stride + col] = D[i];
+                    for (int i = 0; i < 16; ++i) {
+                        const uint32_t b = src[i * rc];
+                        const uint32_t sum = pcal_bits::lop3<pcal_bits::kXor3>(W[i], b, c);
+                        c = pcal_bits::lop3<pcal_bits::kMaj3>(W[i], b, c);
+                        W[i] = sum;
+                    }
+                }
+                if (q == qd) {
+                    uint32_t c = 0;
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const uint32_t b = src[(16 + i) * rc];
+                        const uint32_t sum = pcal_bits::lop3<pcal_bits::kXor3>(D[i], b, c);
+                        c = pcal_bits::lop3<pcal_bits::kMaj3>(D[i], b, c);
+                        D[i] = sum;
+                    }
+                }
+            }
+            if (q == 0) {
+                pcal_bits::transpose16x2(W);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) m[i * a.merge_stride + col] = W[i];
+            }
+            if (q == qd) {
+                pcal_bits::transpose16x2(D);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) m[(16 + i) * a.merge_stride + col] = D[i];
             }
         }
         __syncthreads();
