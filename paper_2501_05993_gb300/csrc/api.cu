@@ -120,12 +120,12 @@ extern "C" int pcal_plan_create(double fs, double f_comb, double f_offset, int N
     const int64_t L = g.L, Nn = g.N;
     if (e == cudaSuccess) {
         if (g.format == PCAL_2BIT) {
-            e = dalloc(&p->d_acc2, L);
-            if (e == cudaSuccess) e = dalloc(&p->d_wide2, 3 * L);
+            e = dalloc(&p->d_acc2, 2 * L);
+            if (e == cudaSuccess) e = dalloc(&p->d_wide2, 2 * 3 * L);
         } else if (g.format == PCAL_I8) {
-            e = dalloc(&p->d_acc8, L);
+            e = dalloc(&p->d_acc8, 2 * L);
         } else {
-            e = dalloc(&p->d_accf, L);
+            e = dalloc(&p->d_accf, 2 * L);
         }
     }
     if (e == cudaSuccess) e = dalloc(&p->d_tw, L);
@@ -135,7 +135,7 @@ extern "C" int pcal_plan_create(double fs, double f_comb, double f_offset, int N
     if (e == cudaSuccess) e = dalloc(&p->d_res, 5 * Nn + 3);
     if (e == cudaSuccess) e = dalloc(&p->d_ticket, 4);
     if (e == cudaSuccess) e = dalloc(&p->d_err, 4);
-    if (e == cudaSuccess) e = dalloc(&p->d_sched, kSchedCounters + 1);
+    if (e == cudaSuccess) e = dalloc(&p->d_sched, kSchedCounters);
     if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&p->h_res), (5 * Nn + 3) * sizeof(double));
     if (e == cudaSuccess) e = launch_init_twiddles(p, 0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(0);
@@ -254,6 +254,7 @@ extern "C" int pcal_finalize_device(pcal_plan* p, void* stream) {
     cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : p->last_stream;
     cudaError_t e = launch_finalize(p, s);
     if (e != cudaSuccess) return cuda_status(e);
+    p->cur ^= 1;  // the next period adds into the other bin set
     p->last_stream = s;
     p->period_start = p->n_abs;
     p->since_spill = 0;
@@ -306,12 +307,12 @@ extern "C" int pcal_get_bins(pcal_plan* p, void* host_out) {
     const int64_t L = p->g.L;
     cudaError_t e = cudaStreamSynchronize(p->last_stream);
     if (e != cudaSuccess) return cuda_status(e);
-    if (p->g.format == PCAL_I8) return cuda_status(cudaMemcpy(host_out, p->d_acc8, L * 8, cudaMemcpyDeviceToHost));
+    if (p->g.format == PCAL_I8) return cuda_status(cudaMemcpy(host_out, cur_acc8(p), L * 8, cudaMemcpyDeviceToHost));
     if (p->g.format == PCAL_F32) {
         // double-float bins -> FP64 on the host
         float* tmp = static_cast<float*>(malloc((size_t)L * 2 * sizeof(float)));
         if (!tmp) return PCAL_ENOMEM;
-        e = cudaMemcpy(tmp, p->d_accf, (size_t)L * 2 * sizeof(float), cudaMemcpyDeviceToHost);
+        e = cudaMemcpy(tmp, cur_accf(p), (size_t)L * 2 * sizeof(float), cudaMemcpyDeviceToHost);
         if (e == cudaSuccess)
             for (int64_t k = 0; k < L; ++k)
                 static_cast<double*>(host_out)[k] = (double)tmp[2 * k] + (double)tmp[2 * k + 1];

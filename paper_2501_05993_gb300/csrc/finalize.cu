@@ -554,10 +554,10 @@ cudaError_t launch_finalize(pcal_plan* p, cudaStream_t s) {
     a.c_l = lv[1] - lv[0];
     a.c_h = lv[2] - lv[0];
     a.c_hl = lv[3] - lv[2] - lv[1] + lv[0];
-    a.acc2 = p->d_acc2;
-    a.wide2 = p->d_wide2;
-    a.acc8 = p->d_acc8;
-    a.accf = p->d_accf;
+    a.acc2 = cur_acc2(p);
+    a.wide2 = cur_wide2(p);
+    a.acc8 = cur_acc8(p);
+    a.accf = cur_accf(p);
     a.tw = p->d_tw;
     a.twN = p->d_twN;
     a.P = reinterpret_cast<float4*>(p->d_P);

@@ -58,8 +58,8 @@ struct BulkArgs {
     int static_boxes; // boxes each CTA takes without the shared counter
     int max_boxes;    // cap per CTA (keeps per-CTA counts below 2^16)
     int chunk;        // boxes per grab from the shared counter
-    unsigned int* sched;  // per column group: boxes handed out dynamically
-    unsigned int* done;   // CTAs finished; the last one resets sched
+    unsigned long long* sched;  // per column group: (epoch << 32) | boxes handed out
+    unsigned int epoch;         // this launch's epoch (never 0)
     int64_t n_rows;
     int64_t k_a;      // phase of the first sample of row 0
     int64_t L;
@@ -171,18 +171,28 @@ struct AccF {
     }
 };
 
-// The last CTA of a launch to finish resets the dynamic box counters for the
-// next launch (stream order makes the reset visible to it).
-__device__ void finish_cta(const BulkArgs& a) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        if (atomicAdd(a.done, 1u) == gridDim.x - 1) {
-            for (int g = 0; g < a.col_groups; ++g) a.sched[g] = 0;
-            *a.done = 0;
-            __threadfence();
+// Hand out `take` boxes of a column group: the counter word is (epoch << 32)
+// | boxes handed out.  The first grab of a launch finds an older epoch and
+// swaps in (epoch, 0); no launch touches the word after its CTAs have started
+// the next launch (they trigger it only once their grabs are done), so no
+// reset is needed.  Returns the first box, or -1 on an inconsistent word.
+__device__ int grab_boxes(unsigned long long* ctr, unsigned int epoch, int take, unsigned int* err) {
+    const unsigned long long mine = (unsigned long long)epoch << 32;
+    unsigned long long cur = atomicAdd(ctr, 0ull);
+    for (int i = 0; (unsigned int)(cur >> 32) != epoch; ++i) {
+        if (i > 1024) {
+            atomicOr(err, PCAL_DERR_SCHED);
+            return -1;
         }
+        const unsigned long long prev = atomicCAS(ctr, cur, mine);
+        cur = prev == cur ? mine : prev;
     }
+    const unsigned long long r = atomicAdd(ctr, (unsigned long long)take);
+    if ((unsigned int)(r >> 32) != epoch) {
+        atomicOr(err, PCAL_DERR_SCHED);
+        return -1;
+    }
+    return (int)(r & 0xffffffffull);
 }
 
 // ---- the kernel ------------------------------------------------------------------
@@ -267,12 +277,15 @@ __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_co
                 if (box >= a.total_boxes) break;
                 ok = issue(box);
             }
-            // the shared counter was reset by the preceding launch: wait for it
-            grid_dependency_wait();
             const int base = a.row_groups * a.static_boxes;
             while (ok && j < a.max_boxes) {
                 const int take = a.chunk < a.max_boxes - j ? a.chunk : a.max_boxes - j;
-                const int v = (int)atomicAdd(&a.sched[cg], (unsigned)take);
+                const int v = grab_boxes(&a.sched[cg], a.epoch, take, a.err);
+                if (v < 0) {
+                    s_failed = 1;
+                    ok = false;
+                    break;
+                }
                 if (base + v >= a.total_boxes) break;
                 for (int c = 0; c < take && ok && base + v + c < a.total_boxes; ++c) ok = issue(base + v + c);
             }
@@ -330,6 +343,9 @@ __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_co
         }
     }
     __syncthreads();
+    // Every grab of this CTA is done: the next launch in the stream may start
+    // (a finalize waits for this kernel; a fold uses a new counter epoch and
+    // adds into the same bins with atomics, or into the other bin set).
     allow_dependents();
     if (s_failed) {
         // Drain: TMA fills whose phase no consumer waited for must land
@@ -339,10 +355,9 @@ __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_co
                 if (s_fill_open[s] && s_last_fill[s] >= 0 &&
                     !mbar_wait(&full[s], (uint32_t)(s_last_fill[s] / a.stages) & 1))
                     atomicOr(a.err, PCAL_DERR_DRAIN_WAIT);
-        finish_cta(a);
+        grid_dependency_wait();
         return;
     }
-    grid_dependency_wait();  // the bins were cleared by the preceding finalize
 
     // ---------------- merge replicas, then flush ----------------
     // The stage buffers are free now (every fill landed and was consumed);
@@ -476,7 +491,9 @@ __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_co
             a.partf[rg * a.cols_total + c0 + tid] = make_float2(s, c);
         }
     }
-    finish_cta(a);
+    // This kernel only completes after the preceding one has, so the
+    // completion order of the stream's kernels stays the launch order.
+    grid_dependency_wait();
 }
 
 // f32: bin k = sum over row groups and over the columns that map to k, in a
@@ -518,8 +535,9 @@ int bits_for(int64_t v) {
 }
 
 // Launched as a programmatic dependent of the preceding kernel: its CTAs may
-// start (and stream their static boxes) while that kernel finishes; they wait
-// for it before touching the box counters and the bins.
+// start while that kernel finishes.  Nothing it touches depends on that
+// kernel (new counter epoch; atomics into the current bin set, which a
+// preceding finalize does not touch); it waits for it only at its very end.
 template <int FMT, int U>
 cudaError_t launch_one(const CUtensorMap& map, const BulkArgs& a, int grid, int block, size_t smem, cudaStream_t s) {
     auto k = bulk_fold_kernel<FMT, U>;
@@ -671,12 +689,13 @@ cudaError_t launch_bulk(pcal_plan* p, const void* d_rows, int64_t n_rows, int64_
     a.max_boxes = t.max_boxes;
     a.chunk = t.chunk;
     a.sched = p->d_sched;
-    a.done = p->d_sched + kSchedCounters;
+    a.epoch = ++p->bulk_epoch;
+    if (a.epoch == 0) a.epoch = ++p->bulk_epoch;  // 0 is the zeroed counters' epoch
     a.n_rows = n_rows;
     a.k_a = k_a;
     a.L = p->g.L;
-    a.acc2 = p->d_acc2;
-    a.acc8 = p->d_acc8;
+    a.acc2 = cur_acc2(p);
+    a.acc8 = cur_acc8(p);
     a.err = p->d_err;
     const int grid = (int)(t.col_groups * t.row_groups);
     cudaError_t e;
@@ -694,7 +713,7 @@ cudaError_t launch_bulk(pcal_plan* p, const void* d_rows, int64_t n_rows, int64_
         e = launch_one<PCAL_F32, 1>(map, a, grid, t.threads, t.smem_bytes, s);
         if (e != cudaSuccess) return e;
         reduce_f32_kernel<<<(unsigned)((p->g.L + 255) / 256), 256, 0, s>>>(p->d_partf, t.row_groups, t.cols_total,
-                                                                           k_a, p->g.L, p->d_accf);
+                                                                           k_a, p->g.L, cur_accf(p));
         *launched = 2;
         p->stats.kernel_launches += 2;
         return cudaGetLastError();

@@ -99,17 +99,17 @@ cudaError_t launch_ragged(pcal_plan* p, const uint8_t* d_bytes, int64_t n, int64
     switch (p->g.format) {
         case PCAL_2BIT: {
             int64_t nb = n / 4;
-            ragged_2bit_kernel<<<grid_for(nb, 256, p->num_sms), 256, 0, s>>>(d_bytes, nb, k0, L, p->d_acc2);
+            ragged_2bit_kernel<<<grid_for(nb, 256, p->num_sms), 256, 0, s>>>(d_bytes, nb, k0, L, cur_acc2(p));
             break;
         }
         case PCAL_I8:
             ragged_i8_kernel<<<grid_for(n, 256, p->num_sms), 256, 0, s>>>(reinterpret_cast<const int8_t*>(d_bytes),
-                                                                            n, k0, L, p->d_acc8);
+                                                                            n, k0, L, cur_acc8(p));
             break;
         default: {
             int64_t g = (L + 255) / 256;
             ragged_f32_kernel<<<(unsigned)g, 256, 0, s>>>(reinterpret_cast<const float*>(d_bytes), n, k0, L,
-                                                          p->d_accf);
+                                                          cur_accf(p));
             break;
         }
     }
@@ -118,7 +118,7 @@ cudaError_t launch_ragged(pcal_plan* p, const uint8_t* d_bytes, int64_t n, int64
 }
 
 cudaError_t launch_spill2(pcal_plan* p, cudaStream_t s) {
-    spill2_kernel<<<grid_for(p->g.L, 256, p->num_sms), 256, 0, s>>>(p->d_acc2, p->d_wide2, p->g.L);
+    spill2_kernel<<<grid_for(p->g.L, 256, p->num_sms), 256, 0, s>>>(cur_acc2(p), cur_wide2(p), p->g.L);
     p->stats.kernel_launches += 1;
     return cudaGetLastError();
 }
@@ -126,7 +126,7 @@ cudaError_t launch_spill2(pcal_plan* p, cudaStream_t s) {
 cudaError_t launch_export_bins(pcal_plan* p, void* d_out, cudaStream_t s) {
     const int64_t L = p->g.L;
     const int64_t n_tot = p->n_abs - p->period_start;
-    export2_kernel<<<grid_for(L, 256, p->num_sms), 256, 0, s>>>(p->d_acc2, p->d_wide2, L, n_tot / L, n_tot % L,
+    export2_kernel<<<grid_for(L, 256, p->num_sms), 256, 0, s>>>(cur_acc2(p), cur_wide2(p), L, n_tot / L, n_tot % L,
                                                                   p->period_start % L,
                                                                   reinterpret_cast<long long*>(d_out));
     p->stats.kernel_launches += 1;

@@ -19,6 +19,7 @@
 #define PCAL_DERR_FULL_WAIT 1u   // a consumer gave up waiting for a tile
 #define PCAL_DERR_EMPTY_WAIT 2u  // the producer gave up waiting for a slot
 #define PCAL_DERR_DRAIN_WAIT 4u  // a CTA gave up draining its copies
+#define PCAL_DERR_SCHED 8u       // the box counter was not in this launch's epoch
 
 // Tile plan of the bulk kernel for a given plan and row count (host only).
 struct BulkTiling {
@@ -63,10 +64,13 @@ struct pcal_plan {
     int64_t since_spill;  // 2-bit: samples added since the last spill
     bool spilled;         // 2-bit: the wide arrays hold counts of this period
     // device state
-    unsigned long long* d_acc2;   // 2-bit packed counts [L]
-    unsigned long long* d_wide2;  // 2-bit spilled counts [3][L]
-    long long* d_acc8;            // int8 sums [L]
-    float2* d_accf;               // float32 sums as double-float (hi, lo) [L]
+    // Bins, in two sets: accumulates add into set `cur`; a finalize drains
+    // set cur and switches cur, so the next period's folds never wait for it.
+    int cur;
+    unsigned long long* d_acc2;   // 2-bit packed counts [2][L]
+    unsigned long long* d_wide2;  // 2-bit spilled counts [2][3][L]
+    long long* d_acc8;            // int8 sums [2][L]
+    float2* d_accf;               // float32 sums as double-float (hi, lo) [2][L]
     float2* d_partf;              // float32 per-tile partial sums (scratch)
     size_t partf_cap;             // capacity of d_partf in float2
     double2* d_tw;                // exp(-j 2 pi m / L), m < L
@@ -76,7 +80,8 @@ struct pcal_plan {
     double* d_res;                // results, 5N+3 doubles
     unsigned int* d_ticket;       // [0] fold ticket, [1] dft ticket
     unsigned int* d_err;          // device error flags
-    unsigned int* d_sched;        // bulk kernel box counters [kSchedCounters] + done count
+    unsigned long long* d_sched;  // bulk kernel box counters [kSchedCounters]: (epoch << 32) | boxes
+    unsigned int bulk_epoch;      // launches of the bulk kernel (epoch of its counters)
     // host
     double* h_res;                // pinned copy of d_res
     void* h_stage[2];             // pinned staging for pcal_accumulate_host
@@ -90,6 +95,12 @@ struct pcal_plan {
     BulkMapEntry map_cache[kBulkMapCache];
     int map_next;
 };
+
+// The bin set that accumulates currently add into.
+inline unsigned long long* cur_acc2(const pcal_plan* p) { return p->d_acc2 + p->cur * p->g.L; }
+inline unsigned long long* cur_wide2(const pcal_plan* p) { return p->d_wide2 + p->cur * 3 * p->g.L; }
+inline long long* cur_acc8(const pcal_plan* p) { return p->d_acc8 + p->cur * p->g.L; }
+inline float2* cur_accf(const pcal_plan* p) { return p->d_accf + p->cur * p->g.L; }
 
 // ---- launchers (return a cudaError_t of the launch) -------------------------
 cudaError_t launch_init_twiddles(pcal_plan* p, cudaStream_t s);
