@@ -246,6 +246,102 @@ int pcal_bulk_tiling(double fs, double f_comb, double f_offset, int N, int sampl
 int pcal_tones_from_counts_noalloc(double fs, double f_comb, double f_offset, int N, const int64_t* d_counts,
                                    int64_t n_samples, const double levels[4], double* d_results, void* stream);
 
+/*
+ * ---- Batches: many channels, one persistent fold launch ----------------------
+ *
+ * A batch holds up to PCAL_MAX_BATCH channels (2-bit or int8 samples), each
+ * with its own fs, f_comb, f_offset and N, hence its own period L (Eq. 4).
+ * One pcal_batch_accumulate call folds a run of samples of every channel with
+ * ONE persistent kernel launch over a work list of all channels' tiles (plus
+ * one small launch for ragged heads and tails, and one that advances the
+ * channels' sample indices); pcal_batch_finalize_device turns every
+ * channel's bins into its N phasors, amplitude, phase and delay (Sec. 2) with
+ * one launch, a thread-block cluster per channel.  The bins are exact
+ * integers, so a channel's counts and phasors do not depend on the batch it
+ * is folded in or on the schedule.  The paper processes one stream at a
+ * time; batching is an interface choice of this library.
+ */
+#define PCAL_MAX_BATCH 4096   /* channels per batch                           */
+#define PCAL_BATCH_MAX_N 256  /* tones per batched channel                    */
+
+typedef struct {
+    double fs, f_comb, f_offset; /* Hz, integral, as for pcal_plan_create     */
+    int N;                       /* fs / f_comb                               */
+    int sample_format;           /* PCAL_2BIT or PCAL_I8                      */
+} pcal_channel_desc;
+
+/* Launch schedule of the persistent fold (pcal_batch_autotune picks one). */
+typedef struct {
+    int ctas;        /* CTAs of the fold launch; 0 = one per SM                */
+    int box_rows;    /* rows per TMA box: 32 or 64                              */
+    int stages;      /* pipeline stages, 0 = as many as fit (at most 8)         */
+    int static_pct;  /* percent of the boxes handed out statically (0..100)     */
+    int min_chunk;   /* smallest dynamic grab, boxes (1..4096)                  */
+    int col_cap;     /* widest column group, 32-bit words: 128 or 224           */
+} pcal_schedule;
+
+typedef struct pcal_batch pcal_batch;
+
+/*
+ * Create a batch on the current device: validates every channel as
+ * pcal_plan_create does (PCAL_EINVAL for an F32 channel, PCAL_ETOOLARGE for
+ * N > PCAL_BATCH_MAX_N), allocates all bins, tables and results in one device
+ * allocation the batch owns, and builds the FP64 rotator tables.  Levels of
+ * 2-bit channels: {-3.3359, -1, +1, +3.3359}.  Synchronous.
+ */
+int pcal_batch_create(const pcal_channel_desc* channels, int n_channels, pcal_batch** out);
+int pcal_batch_destroy(pcal_batch* batch);
+int pcal_batch_get_geometry(const pcal_batch* batch, int channel, pcal_geometry* out);
+int pcal_batch_set_schedule(pcal_batch* batch, const pcal_schedule* sched);
+int pcal_batch_get_schedule(const pcal_batch* batch, pcal_schedule* out);
+
+/*
+ * Fold n[c] more samples of every channel c.  samples: HOST array of
+ * n_channels DEVICE pointers (any alignment; the caller keeps each buffer
+ * valid until the stream passes this call); n: HOST array of sample counts
+ * (0 skips a channel; 2-bit counts are multiples of 4).  Samples continue each
+ * channel's absolute index.  Asynchronous on `stream` (cudaStream_t).
+ */
+int pcal_batch_accumulate(pcal_batch* batch, const void* const* samples, const int64_t* n, void* stream);
+
+/* Finalize every channel on `stream` (results stay on the device) and start
+ * each channel's next period.  Asynchronous. */
+int pcal_batch_finalize_device(pcal_batch* batch, void* stream);
+
+/*
+ * pcal_batch_accumulate + pcal_batch_finalize_device as one CUDA graph: the
+ * first call with a given set of (samples, n) captures the step, later calls
+ * with the same pointers and counts replay it (the buffers' contents may
+ * change).  Every per-step quantity lives on the device, so replays continue
+ * the channels' sample indices correctly.  Asynchronous.
+ */
+int pcal_batch_step_graph(pcal_batch* batch, const void* const* samples, const int64_t* n, void* stream);
+
+/* Results of one channel after a finalize (synchronises the batch's last
+ * stream; PCAL_ETIMEOUT if a device wait gave up).  Layout and NULL handling
+ * as pcal_read_results. */
+int pcal_batch_read_results(pcal_batch* batch, int channel, double* phasors, double* amp, double* phase,
+                            double* unwrapped, double* td, double* sigma);
+
+/* Device address of one channel's result vector (layout of pcal_result_device). */
+int pcal_batch_result_device(const pcal_batch* batch, int channel, const double** out);
+
+/* The current period's exact bins of one channel (synchronises): 2-bit:
+ * int64 [L][4] per-code counts; int8: int64 [L] sums. */
+int pcal_batch_get_bins(pcal_batch* batch, int channel, int64_t* host_out);
+
+int pcal_batch_get_stats(const pcal_batch* batch, pcal_stats* out);
+
+/*
+ * Time candidate schedules (column-width cap, box rows, static share, chunk
+ * size) on these inputs, accumulate only, and keep the fastest; writes it to
+ * *chosen when not NULL.  The batch must be at a period boundary (PCAL_EBUSY
+ * otherwise); its bins are emptied and its indices restored afterwards.
+ * Synchronous.
+ */
+int pcal_batch_autotune(pcal_batch* batch, const void* const* samples, const int64_t* n, void* stream,
+                        pcal_schedule* chosen);
+
 /* Static name of a status code. */
 const char* pcal_strerror(int code);
 

@@ -54,6 +54,22 @@ class Tiling(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ChannelDesc(ctypes.Structure):
+    _fields_ = [("fs", ctypes.c_double), ("f_comb", ctypes.c_double), ("f_offset", ctypes.c_double),
+                ("N", ctypes.c_int), ("sample_format", ctypes.c_int)]
+
+
+class Schedule(ctypes.Structure):
+    _fields_ = [("ctas", ctypes.c_int), ("box_rows", ctypes.c_int), ("stages", ctypes.c_int),
+                ("static_pct", ctypes.c_int), ("min_chunk", ctypes.c_int), ("col_cap", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+PCAL_MAX_BATCH, PCAL_BATCH_MAX_N = 4096, 256
+
+
 class PcalError(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = code
@@ -92,6 +108,19 @@ def load(path: str | None = None):
         "pcal_strerror": ([ci], ctypes.c_char_p),
         "pcal_bulk_tiling": ([dbl, dbl, dbl, ci, ci, ci, i64, P(Tiling)], ci),
         "pcal_tones_from_counts_noalloc": ([dbl, dbl, dbl, ci, vp, i64, P(dbl), vp, vp], ci),
+        "pcal_batch_create": ([P(ChannelDesc), ci, P(vp)], ci),
+        "pcal_batch_destroy": ([vp], ci),
+        "pcal_batch_get_geometry": ([vp, ci, P(Geometry)], ci),
+        "pcal_batch_set_schedule": ([vp, P(Schedule)], ci),
+        "pcal_batch_get_schedule": ([vp, P(Schedule)], ci),
+        "pcal_batch_accumulate": ([vp, P(vp), P(i64), vp], ci),
+        "pcal_batch_finalize_device": ([vp, vp], ci),
+        "pcal_batch_step_graph": ([vp, P(vp), P(i64), vp], ci),
+        "pcal_batch_read_results": ([vp, ci, vp, vp, vp, vp, vp, vp], ci),
+        "pcal_batch_result_device": ([vp, ci, P(vp)], ci),
+        "pcal_batch_get_bins": ([vp, ci, vp], ci),
+        "pcal_batch_get_stats": ([vp, P(Stats)], ci),
+        "pcal_batch_autotune": ([vp, P(vp), P(i64), vp, P(Schedule)], ci),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -291,3 +320,165 @@ class Plan:
     @property
     def result_device_ptr(self) -> int:
         return pcal_result_device(self.handle)
+
+
+# ---- batches ------------------------------------------------------------------------
+
+
+def _ptr_array(samples, count: int):
+    arr = (ctypes.c_void_p * count)(*[_ptr(x) or None for x in samples])
+    return ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p)), arr
+
+
+def _n_array(n, count: int):
+    arr = (ctypes.c_int64 * count)(*[int(v) for v in n])
+    return arr
+
+
+def pcal_batch_create(channels) -> int:
+    """channels: sequence of (fs, f_comb, f_offset, fmt) or (fs, f_comb, f_offset, fmt, N)."""
+    descs = (ChannelDesc * len(channels))()
+    for d, ch in zip(descs, channels):
+        fs, fc, fo, fmt = ch[:4]
+        d.fs, d.f_comb, d.f_offset = float(fs), float(fc), float(fo)
+        d.N = int(ch[4]) if len(ch) > 4 else int(round(fs / fc))
+        d.sample_format = FORMATS[fmt] if isinstance(fmt, str) else int(fmt)
+    h = ctypes.c_void_p()
+    _check(load().pcal_batch_create(descs, len(channels), ctypes.byref(h)), "pcal_batch_create")
+    return h.value
+
+
+def pcal_batch_destroy(batch: int) -> None:
+    _check(load().pcal_batch_destroy(batch), "pcal_batch_destroy")
+
+
+def pcal_batch_get_geometry(batch: int, channel: int) -> Geometry:
+    g = Geometry()
+    _check(load().pcal_batch_get_geometry(batch, channel, ctypes.byref(g)), "pcal_batch_get_geometry")
+    return g
+
+
+def pcal_batch_set_schedule(batch: int, sched: Schedule) -> None:
+    _check(load().pcal_batch_set_schedule(batch, ctypes.byref(sched)), "pcal_batch_set_schedule")
+
+
+def pcal_batch_get_schedule(batch: int) -> Schedule:
+    s = Schedule()
+    _check(load().pcal_batch_get_schedule(batch, ctypes.byref(s)), "pcal_batch_get_schedule")
+    return s
+
+
+def pcal_batch_accumulate(batch: int, samples, n, stream=None) -> None:
+    pp, keep = _ptr_array(samples, len(samples))
+    _check(load().pcal_batch_accumulate(batch, pp, _n_array(n, len(samples)), _stream(stream)),
+           "pcal_batch_accumulate")
+
+
+def pcal_batch_finalize_device(batch: int, stream=None) -> None:
+    _check(load().pcal_batch_finalize_device(batch, _stream(stream)), "pcal_batch_finalize_device")
+
+
+def pcal_batch_step_graph(batch: int, samples, n, stream=None) -> None:
+    pp, keep = _ptr_array(samples, len(samples))
+    _check(load().pcal_batch_step_graph(batch, pp, _n_array(n, len(samples)), _stream(stream)),
+           "pcal_batch_step_graph")
+
+
+def pcal_batch_read_results(batch: int, channel: int, n_tones: int) -> dict:
+    ph = np.empty(2 * n_tones)
+    amp, phase, unw = np.empty(n_tones), np.empty(n_tones), np.empty(n_tones)
+    td, sig = ctypes.c_double(), ctypes.c_double()
+    _check(load().pcal_batch_read_results(batch, channel, ph.ctypes.data, amp.ctypes.data, phase.ctypes.data,
+                                          unw.ctypes.data, ctypes.addressof(td), ctypes.addressof(sig)),
+           "pcal_batch_read_results")
+    return {"phasors": ph[0::2] + 1j * ph[1::2], "amp": amp, "phase": phase, "unwrapped": unw,
+            "td": td.value, "sigma_td": sig.value}
+
+
+def pcal_batch_result_device(batch: int, channel: int) -> int:
+    out = ctypes.c_void_p()
+    _check(load().pcal_batch_result_device(batch, channel, ctypes.byref(out)), "pcal_batch_result_device")
+    return out.value
+
+
+def pcal_batch_get_bins(batch: int, channel: int, geometry: Geometry) -> np.ndarray:
+    if geometry.format == PCAL_2BIT:
+        out = np.empty((geometry.L, 4), dtype=np.int64)
+    else:
+        out = np.empty(geometry.L, dtype=np.int64)
+    _check(load().pcal_batch_get_bins(batch, channel, out.ctypes.data), "pcal_batch_get_bins")
+    return out
+
+
+def pcal_batch_get_stats(batch: int) -> Stats:
+    st = Stats()
+    _check(load().pcal_batch_get_stats(batch, ctypes.byref(st)), "pcal_batch_get_stats")
+    return st
+
+
+def pcal_batch_autotune(batch: int, samples, n, stream=None) -> Schedule:
+    pp, keep = _ptr_array(samples, len(samples))
+    s = Schedule()
+    _check(load().pcal_batch_autotune(batch, pp, _n_array(n, len(samples)), _stream(stream), ctypes.byref(s)),
+           "pcal_batch_autotune")
+    return s
+
+
+class Batch:
+    """Many channels (2-bit or int8) folded by one persistent launch per call."""
+
+    def __init__(self, channels):
+        self.channels = [tuple(c) for c in channels]
+        self.handle = pcal_batch_create(self.channels)
+        self.geometry = [pcal_batch_get_geometry(self.handle, c) for c in range(len(self.channels))]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            pcal_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __len__(self):
+        return len(self.channels)
+
+    def accumulate(self, samples, n, stream=None):
+        pcal_batch_accumulate(self.handle, samples, n, stream)
+
+    def finalize_device(self, stream=None):
+        pcal_batch_finalize_device(self.handle, stream)
+
+    def step_graph(self, samples, n, stream=None):
+        pcal_batch_step_graph(self.handle, samples, n, stream)
+
+    def results(self, channel: int) -> dict:
+        return pcal_batch_read_results(self.handle, channel, int(self.geometry[channel].N))
+
+    def bins(self, channel: int) -> np.ndarray:
+        return pcal_batch_get_bins(self.handle, channel, self.geometry[channel])
+
+    def stats(self) -> dict:
+        return pcal_batch_get_stats(self.handle).as_dict()
+
+    @property
+    def schedule(self) -> dict:
+        return pcal_batch_get_schedule(self.handle).as_dict()
+
+    def set_schedule(self, **kw):
+        s = pcal_batch_get_schedule(self.handle)
+        for k, v in kw.items():
+            setattr(s, k, int(v))
+        pcal_batch_set_schedule(self.handle, s)
+
+    def autotune(self, samples, n, stream=None) -> dict:
+        return pcal_batch_autotune(self.handle, samples, n, stream).as_dict()

@@ -19,10 +19,16 @@
 // every sum over many terms after that uses df (see df64.cuh), which keeps
 // about 48 bits with FP32 instructions.
 //
-// Work split: the fold kernel gives each CTA whole residues b (no two CTAs
-// add into the same P[b]); the last CTA to finish (an atomic ticket, no
-// waiting) runs the DFT for small N and the products.  For large N a second
-// kernel spreads the DFT over CTAs and its last CTA runs the products.
+// Work split.  For N <= 256 and L <= 32768 (every plan of the benchmark
+// workloads) one thread-block cluster does everything: each CTA folds a
+// slice of the bins into a partial P, the partials meet in distributed
+// shared memory, and CTA 0 runs the DFT from shared memory and the products
+// in one warp, so no result makes a round trip through global memory.
+// Otherwise the fold kernel gives each CTA whole residues b (no two CTAs add
+// into the same P[b]); the last CTA to finish (an atomic ticket, no waiting)
+// runs the DFT for small N and the products.  For large N a second kernel
+// spreads the DFT over CTAs and its last CTA runs the products.
+#include <cooperative_groups.h>
 #include <math.h>
 
 #include <mutex>
@@ -423,6 +429,343 @@ __global__ void fin_fold_kernel(FinArgs a) {
     }
 }
 
+// ---- one-cluster finalize (N <= kClusterMaxN) ------------------------------
+
+constexpr int kClusterMaxN = 256;
+constexpr int kClusterThreads = 256;
+constexpr size_t kClusterPadSmem = 28 * 1024;
+constexpr int64_t kClusterMaxL = 32768;
+
+// Exclusive df prefix sum across the 32 lanes of a warp (fixed order).
+__device__ __forceinline__ df warp_exclusive_scan_df(df v) {
+    const int lane = threadIdx.x & 31;
+    df inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const df u{__shfl_up_sync(0xffffffffu, inc.hi, o), __shfl_up_sync(0xffffffffu, inc.lo, o)};
+        if (lane >= o) inc = pcal_df::add(inc, u);
+    }
+    const df prev{__shfl_up_sync(0xffffffffu, inc.hi, 1), __shfl_up_sync(0xffffffffu, inc.lo, 1)};
+    return lane == 0 ? df{0.f, 0.f} : prev;
+}
+
+// K df sums over the 32 lanes by a fixed butterfly; every lane gets them.
+// The steps are a loop, not unrolled: this code runs once per finalize, so
+// its size (instruction fetch) costs more than its loop overhead.
+template <int K>
+__device__ __forceinline__ void warp_sums_df(df (&v)[K]) {
+#pragma unroll 1
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int j = 0; j < K; ++j) v[j] = pcal_df::add(v[j], shfl_xor_df(v[j], o));
+}
+
+// Shared memory of tone_products_warp: per tone the phase, the weight and
+// the unwrapped phase (df).
+struct WarpProductsSmem {
+    float psi[kClusterMaxN];
+    float w[kClusterMaxN];
+    float2 un[kClusterMaxN];
+    float2 out[2];  // td, sigma (df)
+};
+
+// The products of tone_products, by one warp with no block barrier: lane l
+// takes the contiguous tones [l*c, l*c + c), c = ceil(N/32) <= 8.  Loops over
+// a lane's tones are not unrolled, for the reason given at warp_sums_df.
+__device__ __noinline__ void tone_products_warp(const FinArgs& a, const float2* sT, WarpProductsSmem& m) {
+    const int N = (int)a.N;
+    const int lane = threadIdx.x & 31;
+    const int c = (N + 31) / 32;
+    const int i0 = lane * c < N ? lane * c : N;
+    const int i1 = i0 + c < N ? i0 + c : N;
+    // 1. phase and weight per tone, FP32
+#pragma unroll 1
+    for (int i = i0; i < i1; ++i) {
+        const float2 z = sT[i];
+        m.psi[i] = wrap_pi_f(atan2f(z.y, z.x) + 1.5707963267948966f);
+        m.w[i] = z.x * z.x + z.y * z.y;
+    }
+    __syncwarp();
+    // 2. unwrap: u_i = psi_0 + sum_{j=1..i} wrap(psi_j - psi_{j-1}), df sums
+    const int j0 = i0 > 1 ? i0 : 1;
+    df local{0.f, 0.f};
+#pragma unroll 1
+    for (int i = j0; i < i1; ++i) local = pcal_df::add_f(local, wrap_pi_f(m.psi[i] - m.psi[i - 1]));
+    df run = pcal_df::add_f(warp_exclusive_scan_df(local), m.psi[0]);
+#pragma unroll 1
+    for (int i = i0; i < i1; ++i) {
+        if (i > 0) run = pcal_df::add_f(run, wrap_pi_f(m.psi[i] - m.psi[i - 1]));
+        m.un[i] = make_float2(run.hi, run.lo);
+    }
+    // 3. weighted least squares of u_i against the tone index x_i = i (the
+    //    frequency is f_i = f_comb*i + f_offset), weights w_i = |T_i|^2
+    df s3[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll 1
+    for (int i = i0; i < i1; ++i) {
+        const float w = m.w[i];
+        s3[0] = pcal_df::add_f(s3[0], w);
+        s3[1] = pcal_df::add(s3[1], pcal_df::two_prod(w, (float)i));
+        s3[2] = pcal_df::add(s3[2], pcal_df::mul_f(df{m.un[i].x, m.un[i].y}, w));
+    }
+    warp_sums_df<3>(s3);
+    const df W = s3[0];
+    df td{__int_as_float(0x7fc00000), 0.f}, sig{__int_as_float(0x7fc00000), 0.f};  // NaN until fitted
+    if (N >= 2 && W.hi > 0.f) {
+        const df xbar = pcal_df::div(s3[1], W), ubar = pcal_df::div(s3[2], W);
+        // centred sums; the residual sum follows from Syy - slope*Sxu
+        df s2[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll 1
+        for (int i = i0; i < i1; ++i) {
+            const float w = m.w[i];
+            const df dx = pcal_df::sub(df{(float)i, 0.f}, xbar);
+            const df du = pcal_df::sub(df{m.un[i].x, m.un[i].y}, ubar);
+            const df wdx = pcal_df::mul_f(dx, w);
+            s2[0] = pcal_df::add(s2[0], pcal_df::mul(wdx, dx));
+            s2[1] = pcal_df::add(s2[1], pcal_df::mul(wdx, du));
+            s2[2] = pcal_df::add(s2[2], pcal_df::mul_f(pcal_df::mul(du, du), w));
+        }
+        warp_sums_df<3>(s2);
+        if (s2[0].hi > 0.f) {
+            const df slope = pcal_df::div(s2[1], s2[0]);  // rad per tone index
+            td = pcal_df::div(slope, a.two_pi_fc);
+            if (N > 2) {
+                df ssr = pcal_df::sub(s2[2], pcal_df::mul(slope, s2[1]));
+                if (ssr.hi < 0.f) ssr = df{0.f, 0.f};
+                sig = pcal_df::div(pcal_df::sqrt_df(pcal_df::div(ssr, pcal_df::mul_f(s2[0], (float)(N - 2)))),
+                                   a.two_pi_fc);
+            }
+        }
+    }
+    if (lane == 0) {
+        m.out[0] = make_float2(td.hi, td.lo);
+        m.out[1] = make_float2(sig.hi, sig.lo);
+    }
+}
+
+// The FP64 result vector from the products in shared memory, by the block.
+__device__ void write_results_block(const FinArgs& a, const float2* sT, const WarpProductsSmem& m) {
+    const int N = (int)a.N;
+    double* amp = a.res + 2 * N;
+    double* ph = a.res + 3 * N;
+    double* unw = a.res + 4 * N;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const float2 z = sT[i];
+        a.res[2 * i] = (double)z.x;
+        a.res[2 * i + 1] = (double)z.y;
+        amp[i] = (double)(sqrtf(m.w[i]) * a.two_over_m);
+        ph[i] = (double)m.psi[i];
+        unw[i] = (double)m.un[i].x + (double)m.un[i].y;
+    }
+    if (threadIdx.x == 0) {
+        a.res[5 * N] = (double)m.out[0].x + (double)m.out[0].y;
+        a.res[5 * N + 1] = (double)m.out[1].x + (double)m.out[1].y;
+        a.res[5 * N + 2] = a.M;
+    }
+}
+
+// The whole finalize in one cluster of C CTAs.  Thread t of every CTA takes
+// residue b = t % N and every (blockDim/N)-th index m of its CTA's slice
+// [per*r/C, per*(r+1)/C) of m = 0..per-1 (per = L/N), i.e. bins k = b + m*N:
+// consecutive threads read consecutive bins.  Per bin: decode and rotation
+// in FP64 (Eq. 3), then the bin is cleared for the next period.  The lanes of
+// a residue are added in df in shared memory (fixed order).  CTA 0 then adds
+// the C partials of every residue (rank order) read through distributed
+// shared memory, spread over all its threads, and runs the DFT and the
+// products.
+// Runs in every CTA of the cluster; returns true in the CTA that wrote the
+// results (rank 0), after it wrote them.
+__device__ __forceinline__ bool cluster_finalize(const FinArgs& a) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    __shared__ float4 part[kClusterThreads];  // per (lane, residue) df partials: re hi, re lo, im hi, im lo
+    __shared__ float4 Pr[kClusterMaxN];       // this CTA's partial P
+    __shared__ float2 sP[kClusterMaxN], sTw[kClusterMaxN], sT[kClusterMaxN];
+    __shared__ WarpProductsSmem pm;
+    const int C = (int)cluster.num_blocks(), r = (int)cluster.block_rank();
+    const int N = (int)a.N;
+    const int t = threadIdx.x;
+    const int lanes = (int)blockDim.x / N;
+    const int b = t % N, ml = t / N;
+    if (r == 0)
+        for (int i = t; i < N; i += blockDim.x) sTw[i] = a.twN[i];
+    // L <= PCAL_MAX_L: bin and rotator indices fit 32 bits (so*k does not)
+    const int L = (int)a.L;
+    const int64_t so = a.so;
+    const int per = L / N;
+    double re = 0.0, im = 0.0;
+    if (ml < lanes) {
+        const int m1 = per * (r + 1) / C;
+        int m = per * r / C + ml;
+        if (m < m1) {
+            int k = b + m * N;
+            int idx = (int)((so * k) % L);  // rotator index (f_offset/g * k) mod L
+            const int kstep = lanes * N;
+            const int istep = (int)((so * kstep) % L);
+            if (a.fmt == PCAL_2BIT && !a.spilled) {
+                // S = lev0*cnt + c_l*sum(l) + c_h*sum(h) + c_hl*sum(h AND l),
+                // cnt = q or q + 1; the fields are below 2^21
+                const double s_q = a.lev0 * (double)a.q, s_q1 = a.lev0 * (double)(a.q + 1);
+                const int a0 = (int)a.a0, rem = (int)a.rem;
+#pragma unroll 2
+                for (; m < m1; m += lanes) {
+                    const unsigned long long v = a.acc2[k];
+                    const double2 w = a.tw[idx];
+                    a.acc2[k] = 0;
+                    int rr = k - a0;
+                    if (rr < 0) rr += L;
+                    const double S = fma(a.c_hl, (double)(int)((v >> 42) & PCAL_F21_MASK),
+                                         fma(a.c_h, (double)(int)((v >> 21) & PCAL_F21_MASK),
+                                             fma(a.c_l, (double)(int)(v & PCAL_F21_MASK), rr < rem ? s_q1 : s_q)));
+                    re = fma(S, w.x, re);
+                    im = fma(S, w.y, im);
+                    k += kstep;
+                    idx += istep;
+                    if (idx >= L) idx -= L;
+                }
+            } else {
+#pragma unroll 1
+                for (; m < m1; m += lanes) {
+                    const double S = read_bin<false>(a, k);
+                    const double2 w = a.tw[idx];
+                    re = fma(S, w.x, re);
+                    im = fma(S, w.y, im);
+                    clear_bin(a, k);
+                    k += kstep;
+                    idx += istep;
+                    if (idx >= L) idx -= L;
+                }
+            }
+        }
+        const df dre = df_of(re), dim = df_of(im);
+        part[t] = make_float4(dre.hi, dre.lo, dim.hi, dim.lo);
+    }
+    __syncthreads();
+    if (t < N) {
+        df sr{0.f, 0.f}, si{0.f, 0.f};
+#pragma unroll 1
+        for (int l = 0; l < lanes; ++l) {
+            const float4 v = part[l * N + t];
+            sr = pcal_df::add(sr, df{v.x, v.y});
+            si = pcal_df::add(si, df{v.z, v.w});
+        }
+        Pr[t] = make_float4(sr.hi, sr.lo, si.hi, si.lo);
+    }
+    cluster.sync();  // every CTA's partial P is complete
+    if (r == 0) {
+        // thread t: residue t % N, ranks g, g + G, ... (g = t / N, G groups);
+        // the loads are issued together, then added in rank order
+        const int G = lanes < C ? lanes : C;
+        const int g = t / N;
+        if (g < G) {
+            df sr{0.f, 0.f}, si{0.f, 0.f};
+#pragma unroll 1
+            for (int q0 = g; q0 < C; q0 += 4 * G) {
+                float4 v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int q = q0 + u * G;
+                    v[u] = q < C ? *cluster.map_shared_rank(&Pr[t % N], q) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    sr = pcal_df::add(sr, df{v[u].x, v[u].y});
+                    si = pcal_df::add(si, df{v[u].z, v[u].w});
+                }
+            }
+            part[t] = make_float4(sr.hi, sr.lo, si.hi, si.lo);
+        }
+        __syncthreads();
+        if (t < N) {
+            df sr{0.f, 0.f}, si{0.f, 0.f};
+#pragma unroll 1
+            for (int gg = 0; gg < G; ++gg) {
+                const float4 v = part[gg * N + t];
+                sr = pcal_df::add(sr, df{v.x, v.y});
+                si = pcal_df::add(si, df{v.z, v.w});
+            }
+            sP[t] = make_float2(sr.hi + sr.lo, si.hi + si.lo);
+        }
+    }
+    cluster.sync();  // the other CTAs' shared memory is no longer read
+    if (r != 0) return false;
+    // N-point DFT in FP32 from shared memory: g threads per tone
+    int g = 1;
+    while (g < 32 && g * 2 * N <= (int)blockDim.x) g *= 2;
+    const int groups = blockDim.x / g;
+    const int gs = t % g;
+#pragma unroll 1
+    for (int base = 0; base < N; base += groups) {
+        const int i = base + t / g;
+        float sre = 0.f, sim = 0.f;
+        if (i < N) {
+            int ix = (i * gs) % N;
+            const int step = (i * g) % N;
+#pragma unroll 4
+            for (int bb = gs; bb < N; bb += g) {
+                const float2 p = sP[bb];
+                const float2 w = sTw[ix];
+                sre = fmaf(p.x, w.x, fmaf(-p.y, w.y, sre));
+                sim = fmaf(p.x, w.y, fmaf(p.y, w.x, sim));
+                ix += step;
+                if (ix >= N) ix -= N;
+            }
+        }
+        for (int o = g / 2; o > 0; o >>= 1) {
+            sre += __shfl_xor_sync(0xffffffffu, sre, o);
+            sim += __shfl_xor_sync(0xffffffffu, sim, o);
+        }
+        if (i < N && gs == 0) sT[i] = make_float2(sre, sim);
+    }
+    __syncthreads();
+    if (t < 32) tone_products_warp(a, sT, pm);
+    __syncthreads();
+    write_results_block(a, sT, pm);
+    return true;
+}
+
+__global__ void __launch_bounds__(kClusterThreads) fin_cluster_kernel(FinArgs a) {
+    // The next fold may launch at once: it adds into the other set of bins
+    // and waits for this kernel before its first atomic.
+    allow_dependents();
+    grid_dependency_wait();  // the bins of the preceding fold
+    cluster_finalize(a);
+}
+
+// Batch finalize: cluster c finalizes channel c of the batch from the
+// channel's device state, then starts the channel's next period.
+__global__ void __launch_bounds__(kClusterThreads) batch_fin_kernel(BatchChan* ch) {
+    namespace cg = cooperative_groups;
+    const int c = (int)(blockIdx.x / cg::this_cluster().num_blocks());
+    BatchChan& bc = ch[c];
+    const int64_t n_tot = bc.n_abs - bc.period_start;
+    FinArgs a{};
+    a.fmt = bc.fmt;
+    a.spilled = 1;  // 2-bit sums live in the wide arrays; the packed words are zero
+    a.L = bc.L;
+    a.N = bc.N;
+    a.so = bc.so;
+    a.q = n_tot / bc.L;
+    a.rem = n_tot % bc.L;
+    a.a0 = bc.period_start % bc.L;
+    a.lev0 = bc.lev0;
+    a.c_l = bc.c_l;
+    a.c_h = bc.c_h;
+    a.c_hl = bc.c_hl;
+    a.M = (double)n_tot;
+    a.two_over_m = n_tot > 0 ? (float)(2.0 / (double)n_tot) : 0.0f;
+    a.two_pi_fc.hi = (float)bc.two_pi_fc;
+    a.two_pi_fc.lo = (float)(bc.two_pi_fc - (double)a.two_pi_fc.hi);
+    a.acc2 = bc.zero2;
+    a.wide2 = bc.wide2;
+    a.acc8 = bc.acc8;
+    a.tw = bc.tw;
+    a.twN = bc.twN;
+    a.res = bc.res;
+    // every CTA has read the state above before the first cluster barrier
+    // inside, and rank 0 returns after the last one
+    if (cluster_finalize(a) && threadIdx.x == 0) bc.period_start = bc.n_abs;
+}
+
 // Spread DFT for large N; the last CTA runs the products.
 template <bool NoAlloc>
 __global__ void fin_dft_kernel(FinArgs a) {
@@ -526,6 +869,96 @@ cudaError_t launch_finalize_args(FinArgs a, int num_sms, cudaStream_t s, int* la
     return e;
 }
 
+// Cluster size for fin_cluster_kernel on the current device: 16 CTAs where
+// the device can co-schedule them (a non-portable size), else the portable
+// 8; 0 when no cluster fits.  Evaluated once per device.
+int cluster_size_for_device() {
+    static std::mutex mu;
+    static int cached[64];
+    static bool known[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (known[dev]) return cached[dev];
+    int best = 0;
+    if (cudaFuncSetAttribute(fin_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+        (void)cudaGetLastError();
+    for (int c : {16, 8}) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(c);
+        cfg.blockDim = dim3(kClusterThreads);
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = c;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, fin_cluster_kernel, &cfg) == cudaSuccess && n > 0) {
+            best = c;
+            break;
+        }
+        (void)cudaGetLastError();
+    }
+    cached[dev] = best;
+    known[dev] = true;
+    return best;
+}
+
+// One cluster of C CTAs as a programmatic dependent of the preceding kernel.
+// The CTAs ask for kClusterPadSmem more shared memory than they use, so that
+// none of them fits on an SM beside a CTA of the fold that overlaps it (about
+// 205 KB each): sharing an SM with a fold CTA slowed the finalize 2-3x.  The
+// fold leaves kFinalizeReserveSms SMs for it.
+cudaError_t launch_cluster_finalize(const FinArgs& a, int C, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(kClusterThreads);
+    cfg.dynamicSmemBytes = kClusterPadSmem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    attr[1].id = cudaLaunchAttributeClusterDimension;
+    attr[1].val.clusterDim.x = C;
+    attr[1].val.clusterDim.y = 1;
+    attr[1].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    return cudaLaunchKernelEx(&cfg, fin_cluster_kernel, a);
+}
+
+}  // namespace
+
+cudaError_t prepare_batch_finalize() {
+    const int C = cluster_size_for_device();
+    if (C == 0) return cudaErrorNotSupported;
+    return C > 8 ? cudaFuncSetAttribute(batch_fin_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)
+                 : cudaSuccess;
+}
+
+// prepare_batch_finalize() must have succeeded on this device (it makes the
+// CUDA calls that a stream capture does not allow).
+cudaError_t launch_batch_finalize(BatchChan* d_ch, int n_ch, cudaStream_t s) {
+    const int C = cluster_size_for_device();
+    if (C == 0) return cudaErrorNotSupported;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(n_ch * C);
+    cfg.blockDim = dim3(kClusterThreads);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, batch_fin_kernel, d_ch);
+}
+
+namespace {
+
 void set_common(FinArgs& a, const pcal_geometry& g, int64_t n_tot) {
     a.L = g.L;
     a.N = g.N;
@@ -564,6 +997,13 @@ cudaError_t launch_finalize(pcal_plan* p, cudaStream_t s) {
     a.T = reinterpret_cast<float2*>(p->d_T);
     a.res = p->d_res;
     a.ticket = p->d_ticket;
+    if (g.N <= kClusterMaxN && g.L <= kClusterMaxL) {
+        const int C = cluster_size_for_device();
+        if (C > 0) {
+            p->stats.kernel_launches += 1;
+            return launch_cluster_finalize(a, C, s);
+        }
+    }
     int launches = 0;
     cudaError_t e = launch_finalize_args<false>(a, p->num_sms, s, &launches);
     p->stats.kernel_launches += launches;

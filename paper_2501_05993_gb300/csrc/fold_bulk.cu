@@ -34,12 +34,12 @@
 #include "bitplane.cuh"
 #include "df64.cuh"
 #include "internal.cuh"
+#include "ptx.cuh"
 
 namespace {
 
 constexpr int kMaxBlock = 640;           // consumer warps + producer warp (<= 96 registers)
 constexpr int kSmemBudget = 220 * 1024;  // dynamic shared memory per CTA
-constexpr uint64_t kWaitLimitNs = 2000000000ull;  // give up a wait after 2 s
 
 struct BulkArgs {
     int cols_total;   // words per row
@@ -69,69 +69,7 @@ struct BulkArgs {
     unsigned int* err;
 };
 
-// ---- PTX wrappers -------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void fence_barrier_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-
-// Programmatic dependent launch: wait for the preceding kernel's results;
-// allow the following kernel to start launching.
-__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
-// try_wait suspends the thread in hardware for a while instead of spinning.
-__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Wait for the phase of `parity` to complete; false after kWaitLimitNs.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    if (mbar_try(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
-    while (!mbar_try(bar, parity))
-        if (global_ns() - t0 > kWaitLimitNs) return false;
-    return true;
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
-        : "memory");
-}
-
+using namespace pcal_ptx;
 
 // ---- per-format consumer state --------------------------------------------------
 
@@ -437,6 +375,10 @@ __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_co
             }
         }
         __syncthreads();
+        // The bins this fold adds into were cleared by the finalize two
+        // kernels back; waiting for the preceding kernel here (it waited for
+        // its own predecessor) orders these atomics after that clearing.
+        grid_dependency_wait();
         // one atomic per (column, sample): consecutive threads, consecutive bins
         const int S = a.merge_stride;
         const int tasks = a.col_width * 16;
@@ -466,6 +408,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_co
                 if (acc8.s[j]) atomicAdd(&m[j * S + col], acc8.s[j]);
         }
         __syncthreads();
+        grid_dependency_wait();  // as for the 2-bit flush
         for (int t = tid; t < a.col_width * 4; t += blockDim.x) {
             const int cl = t >> 2, j = t & 3;
             const int gc = c0 + cl;
@@ -492,7 +435,8 @@ __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_co
         }
     }
     // This kernel only completes after the preceding one has, so the
-    // completion order of the stream's kernels stays the launch order.
+    // completion order of the stream's kernels stays the launch order (a
+    // second wait returns at once).
     grid_dependency_wait();
 }
 
@@ -612,13 +556,15 @@ int bulk_tiling(const pcal_plan* p, int64_t n_rows, BulkTiling* t) {
     z.stages = stages;
     z.merge_stride = ms;
     // Work split: boxes of one column group are shared by row_groups CTAs
-    // (one wave over the SMs): a static share each, the rest handed out in
-    // chunks from a counter; each CTA takes at most max_boxes (twice the
-    // average), which keeps its 16-bit per-position counts below 2^16.
+    // (one wave over the SMs the finalize does not need): a static share
+    // each, the rest handed out in chunks from a counter; each CTA takes at
+    // most max_boxes (twice the average), which keeps its 16-bit
+    // per-position counts below 2^16.
     const int64_t total = (n_rows + box - 1) / box;
     if (total > 0x3fffffff) return -1;
     const int64_t cap = 65535 / box;
-    int64_t gr = p->num_sms / gc;
+    const int sms = p->num_sms >= 64 ? p->num_sms - kFinalizeReserveSms : p->num_sms;
+    int64_t gr = sms / gc;
     if (gr < 1) gr = 1;
     if (gr > total) gr = total;
     while ((total + gr - 1) / gr * 2 > cap) ++gr;  // very long inputs: more CTAs

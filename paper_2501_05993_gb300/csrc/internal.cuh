@@ -50,6 +50,9 @@ struct BulkMapEntry {
     CUtensorMap map;
 };
 constexpr int kBulkMapCache = 16;
+// SMs the bulk fold leaves free (on GPUs with at least 64 SMs) for the
+// one-cluster finalize that overlaps it.
+constexpr int kFinalizeReserveSms = 16;
 constexpr int kSchedCounters = 8192;  // dynamic box counters (one per column group) + 1
 
 struct pcal_plan {
@@ -117,3 +120,52 @@ cudaError_t launch_bulk(pcal_plan* p, const void* d_rows, int64_t n_rows, int64_
                         int* launched);
 
 int bulk_tiling(const pcal_plan* p, int64_t n_rows, BulkTiling* t);
+
+// ---- batches (pcal_batch_*) ------------------------------------------------------
+
+// One channel of a batch in device memory: its constants, its bins and its
+// running sample index.  The kernels advance the index themselves, so a
+// captured step can be replayed without the host.
+struct BatchChan {
+    int fmt;              // PCAL_2BIT or PCAL_I8
+    int spw;              // samples per 32-bit word (16 or 4)
+    int N;
+    int L;
+    int64_t so;           // rotator index step per sample: f_offset/g (mod L)
+    int cols_total;       // words per bulk row
+    int col_width;        // words per column group (the TMA box width)
+    int col_groups;
+    int64_t row_samples;  // samples per bulk row (a multiple of L)
+    unsigned long long* zero2;  // 2-bit: L zero words (the packed fields of the single-plan layout)
+    unsigned long long* wide2;  // 2-bit: [3][L] sums of l, h and (h AND l)
+    long long* acc8;            // int8: [L] sums
+    const double2* tw;          // exp(-j 2 pi m / L), m < L
+    const float2* twN;          // exp(-j 2 pi m / N), m < N
+    double* res;                // 5N+3 results
+    double lev0, c_l, c_h, c_hl;
+    double two_pi_fc;
+    long long n_abs;            // samples accumulated since creation
+    long long period_start;     // absolute index of the current period's first sample
+};
+
+// One (channel, column group) of one accumulate call's bulk rows.
+struct BatchSeg {
+    long long box_start;  // first box in the call's box sequence
+    int n_boxes;
+    int ch;
+    int col0;             // first word column of the group
+    int tx_bytes;         // bytes one box delivers
+    long long head;       // samples of the call before its first bulk row
+};
+
+// A ragged run (head or tail) of one accumulate call.
+struct BatchPiece {
+    const uint8_t* ptr;   // its first byte
+    long long n;          // samples
+    long long off;        // offset of its first sample within the call
+    int ch;
+    int pad;
+};
+
+cudaError_t prepare_batch_finalize();
+cudaError_t launch_batch_finalize(BatchChan* d_ch, int n_ch, cudaStream_t s);

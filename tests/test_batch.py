@@ -1,0 +1,217 @@
+"""Batched extraction (pcal_batch_*) against the FP64 CPU oracle.
+
+Every channel of a batch -- mixed 2-bit and int8, different fs, f_offset,
+period L and length, misaligned device buffers, channels too short for a
+bulk row and empty channels -- must give exactly the oracle's integer bins
+and phasors within the stated tolerance, whatever the launch schedule, and
+the same through a replayed CUDA graph.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+PHASOR_RTOL = 1e-5
+
+# (fs, f_comb, f_offset, format, samples, byte offset of the device buffer)
+CHANNELS = [
+    (64_000_000, 1_000_000, 10_000, "2bit", 4 * 1_003_217, 3),   # L 6400
+    (32_000_000, 1_000_000, 0, "i8", 1_500_011, 5),              # f_offset 0: L = N = 32
+    (128_000_000, 1_000_000, 370_000, "2bit", 4 * 901_237, 0),   # L 12800
+    (256_000_000, 1_000_000, 990_000, "i8", 2_600_003, 11),      # L 25600
+    (32_000_000, 1_000_000, 500_000, "2bit", 4 * 500_001, 7),    # f_offset = f_comb/2: L 64
+    (16, 4, 1, "i8", 40_000, 1),                                 # L 16, N 4
+    (64_000_000, 1_000_000, 20_000, "2bit", 4 * 1_000, 2),       # too short for one bulk row
+    (128_000_000, 1_000_000, 50_000, "i8", 0, 0),                # empty this period
+]
+
+
+@pytest.fixture(scope="module")
+def pcal():
+    import torch
+
+    from paper_2501_05993_gb300 import build as libbuild
+
+    libbuild.build()
+    import paper_2501_05993_gb300 as pkg
+
+    pkg.load()
+    torch.cuda.set_device(0)
+    return pkg
+
+
+def to_dev(host: np.ndarray, offset: int = 0):
+    import torch
+
+    raw = host.view(np.uint8)
+    buf = torch.zeros(raw.size + 512, dtype=torch.uint8, device="cuda")
+    base = buf.data_ptr()
+    start = ((base + 255) // 256 * 256 - base) + offset
+    if raw.size:
+        buf[start:start + raw.size].copy_(torch.from_numpy(raw))
+    return buf, base + start
+
+
+def make_inputs(channels, seed=5, n0=None):
+    hosts = []
+    for i, (fs, fc, fo, fmt, n, _) in enumerate(channels):
+        s = synth.Stream(fs=fs, fc=fc, fo=fo, amp=0.05, td=3e-9 * (i + 1) if fs > 1000 else 0.01, seed=seed,
+                         stream=i)
+        hosts.append(s.samples(fmt, 0 if n0 is None else n0[i], n))
+    return hosts
+
+
+def upload(channels, hosts):
+    keep, ptrs = [], []
+    for (fs, fc, fo, fmt, n, off), h in zip(channels, hosts):
+        k, a = to_dev(h, off)
+        keep.append(k)
+        ptrs.append(a)
+    return keep, ptrs
+
+
+def check_channel(batch, c, ch, host, n0=0):
+    fs, fc, fo, fmt, n, _ = ch
+    L = int(batch.geometry[c].L)
+    bins = batch.bins(c)
+    if fmt == "2bit":
+        ref = oracle.counts_2bit(host, n0, L)
+    else:
+        ref = oracle.sums_i8(host, n0, L)
+    assert np.array_equal(bins, ref), f"channel {c}: bins differ at {np.argwhere(bins != ref)[:4].tolist()}"
+    return bins
+
+
+def check_results(batch, c, ch, host, n0=0):
+    fs, fc, fo, fmt, n, _ = ch
+    res = batch.results(c)
+    if n == 0:
+        return res  # no samples this period: nothing to compare
+    L = int(batch.geometry[c].L)
+    S = oracle.bins(host, fmt, n0, L)
+    ref = oracle.tones_from_bins(S, fs, fc, fo)
+    T = res["phasors"]
+    scale = np.max(np.abs(ref))
+    assert np.max(np.abs(T - ref)) <= PHASOR_RTOL * scale, (c, np.max(np.abs(T - ref)) / scale)
+    assert np.allclose(res["amp"], 2 * np.abs(T) / n, rtol=1e-6)
+    return res
+
+
+def test_batch_bins_and_phasors(pcal):
+    hosts = make_inputs(CHANNELS)
+    keep, ptrs = upload(CHANNELS, hosts)
+    with pcal.Batch([c[:4] for c in CHANNELS]) as b:
+        b.accumulate(ptrs, [c[4] for c in CHANNELS])
+        st = b.stats()
+        assert st["bulk_launches"] == 1  # one persistent launch for every channel
+        for c, (ch, h) in enumerate(zip(CHANNELS, hosts)):
+            check_channel(b, c, ch, h)
+        b.finalize_device()
+        for c, (ch, h) in enumerate(zip(CHANNELS, hosts)):
+            check_results(b, c, ch, h)
+
+
+@pytest.mark.parametrize("sched", [
+    dict(ctas=152, box_rows=32, static_pct=0, min_chunk=1, col_cap=224),
+    dict(ctas=37, box_rows=64, static_pct=100, min_chunk=8, col_cap=128),
+    dict(ctas=300, box_rows=32, static_pct=60, min_chunk=3, col_cap=128, stages=3),
+])
+def test_batch_schedule_does_not_change_bins(pcal, sched):
+    hosts = make_inputs(CHANNELS, seed=9)
+    keep, ptrs = upload(CHANNELS, hosts)
+    with pcal.Batch([c[:4] for c in CHANNELS]) as b:
+        b.set_schedule(**sched)
+        b.accumulate(ptrs, [c[4] for c in CHANNELS])
+        for c, (ch, h) in enumerate(zip(CHANNELS, hosts)):
+            check_channel(b, c, ch, h)
+
+
+def test_batch_matches_single_channel_plans(pcal):
+    """The same channels one plan at a time give the same exact bins and
+    phasors within the tolerance."""
+    hosts = make_inputs(CHANNELS[:4], seed=21)
+    keep, ptrs = upload(CHANNELS[:4], hosts)
+    with pcal.Batch([c[:4] for c in CHANNELS[:4]]) as b:
+        b.accumulate(ptrs, [c[4] for c in CHANNELS[:4]])
+        bb = [b.bins(c) for c in range(4)]
+        b.finalize_device()
+        rb = [b.results(c) for c in range(4)]
+    for c, (fs, fc, fo, fmt, n, off) in enumerate(CHANNELS[:4]):
+        with pcal.Plan(fs, fc, fo, fmt) as p:
+            p.accumulate(ptrs[c], n)
+            assert np.array_equal(p.bins(), bb[c])
+            T = p.finalize()
+        scale = np.max(np.abs(T))
+        assert np.max(np.abs(rb[c]["phasors"] - T)) <= PHASOR_RTOL * scale
+
+
+def test_batch_two_calls_and_two_periods(pcal):
+    """Chunks continue each channel's sample index; a finalize starts the
+    next period with empty bins."""
+    chans = CHANNELS[:6]
+    hosts = make_inputs(chans, seed=33)
+    cut = [((ch[4] // 3) // 4) * 4 for ch in chans]
+    first = [h[:c // 4] if ch[3] == "2bit" else h[:c] for h, c, ch in zip(hosts, cut, chans)]
+    second = [h[c // 4:] if ch[3] == "2bit" else h[c:] for h, c, ch in zip(hosts, cut, chans)]
+    with pcal.Batch([c[:4] for c in chans]) as b:
+        k1, p1 = upload(chans, first)
+        b.accumulate(p1, cut)
+        k2, p2 = upload([(c[0], c[1], c[2], c[3], c[4], (c[5] + 6) % 16) for c in chans], second)
+        b.accumulate(p2, [ch[4] - c for ch, c in zip(chans, cut)])
+        for c, (ch, h) in enumerate(zip(chans, hosts)):
+            check_channel(b, c, ch, h)
+        b.finalize_device()
+        for c, (ch, h) in enumerate(zip(chans, hosts)):
+            check_results(b, c, ch, h)
+        # period 2 starts at each channel's absolute index n
+        hosts2 = make_inputs(chans, seed=34, n0=[ch[4] for ch in chans])
+        k3, p3 = upload(chans, hosts2)
+        b.accumulate(p3, [ch[4] for ch in chans])
+        for c, (ch, h) in enumerate(zip(chans, hosts2)):
+            check_channel(b, c, ch, h, n0=ch[4])
+        b.finalize_device()
+        for c, (ch, h) in enumerate(zip(chans, hosts2)):
+            check_results(b, c, ch, h, n0=ch[4])
+
+
+def test_batch_graph_replay(pcal):
+    """A captured step replayed on refilled buffers gives each period's
+    oracle results."""
+    import torch
+
+    chans = CHANNELS[:6]
+    with pcal.Batch([c[:4] for c in chans]) as b:
+        hosts = make_inputs(chans, seed=40)
+        keep, ptrs = upload(chans, hosts)
+        n = [ch[4] for ch in chans]
+        for period in range(3):
+            if period:
+                n0 = [period * ch[4] for ch in chans]
+                hosts = make_inputs(chans, seed=40 + period, n0=n0)
+                for k, h, ch in zip(keep, hosts, chans):
+                    raw = torch.from_numpy(h.view(np.uint8))
+                    base = k.data_ptr()
+                    start = ((base + 255) // 256 * 256 - base) + ch[5]
+                    if raw.numel():
+                        k[start:start + raw.numel()].copy_(raw)
+            b.step_graph(ptrs, n)
+            for c, (ch, h) in enumerate(zip(chans, hosts)):
+                check_results(b, c, ch, h, n0=period * ch[4])
+
+
+def test_batch_autotune_keeps_results(pcal):
+    hosts = make_inputs(CHANNELS, seed=50)
+    keep, ptrs = upload(CHANNELS, hosts)
+    n = [c[4] for c in CHANNELS]
+    with pcal.Batch([c[:4] for c in CHANNELS]) as b:
+        chosen = b.autotune(ptrs, n)
+        assert chosen["box_rows"] in (32, 64) and chosen["col_cap"] in (128, 224)
+        assert b.schedule == chosen
+        for c in range(len(CHANNELS)):  # bins emptied again
+            assert not np.any(b.bins(c)[:, 1:] if CHANNELS[c][3] == "2bit" else b.bins(c))
+        b.accumulate(ptrs, n)
+        for c, (ch, h) in enumerate(zip(CHANNELS, hosts)):
+            check_channel(b, c, ch, h)

@@ -83,6 +83,7 @@ PLANS = {
     "image": (32_000_000, 1_000_000, 500_000),   # L = 64, f_offset = f_comb / 2
     "wide": (1_024_000_000, 1_000_000, 10_000),  # L = 102400, 25 column groups
     "odd": (48_000_000, 1_000_000, 30_000),      # L = 1600, N = 48
+    "long": (256_000_000, 1_000_000, 1_000),     # L = 256000, N = 256: finalize by completion ticket
 }
 
 
