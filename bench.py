@@ -417,7 +417,9 @@ def run_batch(args):
     dev = torch.cuda.current_device()
     libbuild.build()
     pcal.load()
-    chans = batch_channels()
+    chans = batch_channels(args.batch_channels)
+    for c in chans:  # a smaller case of the same workload (profiling)
+        c["n"] = max(4 * c["fs"] // 100, int(c["n"] * args.batch_scale) // (c["fs"] // 100) * (c["fs"] // 100))
     batch = pcal.Batch([(c["fs"], c["fc"], c["fo"], c["fmt"]) for c in chans])
     bufs, blocks = batch_inputs(chans, batch.geometry)
     ptrs = [b.data_ptr() for b in bufs]
@@ -560,6 +562,138 @@ def run_batch(args):
         dist.destroy_process_group()
 
 
+# ---- serving workload: 256 live streams, 10 ms chunks, Poisson arrivals ------------------
+
+SERVE_SEED = 2501059932 + 3
+SERVE_WORKLOAD = ("256 streams, fs in {32, 64, 128, 256, 512, 1024} MHz, f_comb 1 MHz, f_offset 10 kHz x U{0..99}, "
+                  "even streams 2-bit, odd int8 (sigma 20), 10 ms chunks with Poisson arrivals (mean 10 ms per "
+                  "stream), 40 GB HBM admission budget, phasors every 1 s")
+
+
+def serve_streams(n_streams: int):
+    rng = np.random.default_rng(SERVE_SEED)
+    out = []
+    for i in range(n_streams):
+        fs = int(rng.choice([32, 64, 128, 256, 512, 1024])) * 1_000_000
+        out.append({"fs": fs, "fc": 1_000_000, "fo": 10_000 * int(rng.integers(0, 100)),
+                    "fmt": "2bit" if i % 2 == 0 else "i8", "amp": float(rng.uniform(0.005, 0.02)),
+                    "td": float(rng.uniform(0.0, 50e-9)), "id": i})
+    return out
+
+
+def serve_chunks(st, k_chunks: int, chunk_s: float):
+    """k distinct pinned chunks of chunk_s seconds (whole periods L: the comb stays coherent when they repeat)."""
+    import torch
+
+    import synth
+
+    n = int(st["fs"] * chunk_s)
+    s = synth.Stream(fs=st["fs"], fc=st["fc"], fo=st["fo"], amp=st["amp"], td=st["td"], seed=SERVE_SEED,
+                     stream=1000 * st["id"])
+    raw = s.samples(st["fmt"], 0, n * k_chunks).view(np.uint8)
+    nb = raw.size // k_chunks
+    out = []
+    for k in range(k_chunks):
+        t = torch.from_numpy(raw[k * nb:(k + 1) * nb].copy()).pin_memory()
+        out.append((t, t.numpy(), n))
+    return out
+
+
+def run_serve(args):
+    import torch
+
+    import paper_2501_05993_gb300 as pcal
+    from paper_2501_05993_gb300 import build as libbuild
+
+    rank, world, local = rank_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    libbuild.build()
+    pcal.load()
+    chunk_s, period_s = 0.01, 1.0
+    streams = serve_streams(args.serve_streams)
+    pools = [serve_chunks(st, 2, chunk_s) for st in streams]
+    rate = sum(st["fs"] * (0.25 if st["fmt"] == "2bit" else 1.0) for st in streams)  # bytes/s offered
+    srv = pcal.Server(args.serve_budget_gb << 30, len(streams), period_s, 0.1)
+    ids = [srv.open(st["fs"], st["fc"], st["fo"], st["fmt"]) for st in streams]
+    rng = np.random.default_rng(SERVE_SEED + 1)
+
+    # real time: each stream's chunks arrive as a Poisson process (mean chunk_s);
+    # due chunks are submitted together every tick
+    clocks = ClockSampler(dev)
+    clocks.start()
+    t0 = time.perf_counter()
+    next_t = t0 + rng.exponential(chunk_s, len(streams))
+    sent = np.zeros(len(streams), dtype=np.int64)
+    lag_max = 0.0
+    duration = args.serve_seconds
+    while True:
+        now = time.perf_counter()
+        if now - t0 >= duration:
+            break
+        due = np.nonzero(next_t <= now)[0]
+        if due.size == 0:
+            time.sleep(max(0.0, min(next_t.min() - now, 0.001)))
+            continue
+        lag_max = max(lag_max, float(now - next_t[due].min()))
+        srv.submit_many([ids[i] for i in due], [pools[i][sent[i] % 2][1] for i in due],
+                        [pools[i][sent[i] % 2][2] for i in due])
+        sent[due] += 1
+        next_t[due] += rng.exponential(chunk_s, due.size)
+    t_rt = time.perf_counter() - t0
+    srv.drain(120)
+    clk = clocks.stop()
+    rt = srv.stats()
+    lat = []
+    while True:
+        r = srv.poll(0.0)
+        if r is None:
+            break
+        lat.append(r["latency_s"])
+    rt_samples = int(sum(sent[i] * pools[i][0][2] for i in range(len(streams))))
+
+    # saturation: every stream submits its next second of chunks as fast as the
+    # rings and the GPU take them
+    s0 = srv.stats()
+    t1 = time.perf_counter()
+    per = int(period_s / chunk_s)
+    for k in range(per * args.serve_sat_periods):
+        srv.submit_many(ids, [pools[i][k % 2][1] for i in range(len(streams))],
+                        [pools[i][k % 2][2] for i in range(len(streams))])
+    srv.drain(300)
+    t_sat = time.perf_counter() - t1
+    s1 = srv.stats()
+    sat_samples = s1["samples"] - s0["samples"]
+    sat_bytes = s1["bytes_h2d"] - s0["bytes_h2d"]
+    srv.close()
+    lat.sort()
+    p50 = lat[(len(lat) - 1) // 2] if lat else None
+    p99 = lat[int((len(lat) - 1) * 0.99)] if lat else None
+    if rank == 0:
+        out = {
+            "metric": "PCal serving p99 latency (last chunk of a 1 s period submitted -> phasors on the host)",
+            "value": p99 * 1e3 if p99 is not None else None, "unit": "ms", "n_gpus": world, "steps": len(lat),
+            "warmup": 0, "ms_per_step": None, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic",
+            "config": {"workload": SERVE_WORKLOAD, "streams": len(streams), "offered_GBps": rate / 1e9,
+                       "realtime_seconds": t_rt, "max_submit_lag_s": lag_max, "hbm_budget_GB": args.serve_budget_gb,
+                       "chunk_pool": "2 distinct seeded chunks per stream, repeated"},
+            "p50_ms": p50 * 1e3 if p50 is not None else None, "p99_ms": p99 * 1e3 if p99 is not None else None,
+            "periods": len(lat),
+            "realtime": {"value": rt_samples / t_rt / 1e9, "unit": UNIT, "launches": rt["launches"],
+                         "admitted": rt["admitted"], "hbm_in_use_GB": rt["hbm_in_use"] / 2**30},
+            "saturation": {"value": sat_samples / t_sat / 1e9, "unit": UNIT, "h2d_GBps": sat_bytes / t_sat / 1e9,
+                           "seconds": t_sat, "periods_per_stream": args.serve_sat_periods},
+            "e2e": {"value": sat_samples / t_sat / 1e9, "unit": UNIT, "h2d_bytes_per_step": sat_bytes,
+                    "d2h_bytes_per_step": sum((5 * int(round(st["fs"] / st["fc"])) + 3) * 8 for st in streams)},
+            "clocks": clk,
+        }
+        print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -571,7 +705,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=64_000_000)
     ap.add_argument("--ref-sample", type=int, default=8_000_000)
-    ap.add_argument("--workload", default="single", choices=["single", "batch"],
+    ap.add_argument("--batch-channels", type=int, default=64)
+    ap.add_argument("--batch-scale", type=float, default=1.0, help="batch workload: scale every channel's length")
+    ap.add_argument("--serve-streams", type=int, default=256)
+    ap.add_argument("--serve-seconds", type=float, default=4.0, help="serve workload: real-time phase, seconds")
+    ap.add_argument("--serve-sat-periods", type=int, default=2)
+    ap.add_argument("--serve-budget-gb", type=int, default=40)
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve"],
                     help="single: the 2-bit single-channel headline workload; batch: 64 mixed channels")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -580,6 +720,8 @@ def main():
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_gpu(args)
 

@@ -262,7 +262,7 @@ int pcal_tones_from_counts_noalloc(double fs, double f_comb, double f_offset, in
  * time; batching is an interface choice of this library.
  */
 #define PCAL_MAX_BATCH 4096   /* channels per batch                           */
-#define PCAL_BATCH_MAX_N 256  /* tones per batched channel                    */
+#define PCAL_BATCH_MAX_N 1024 /* tones per batched channel                    */
 
 typedef struct {
     double fs, f_comb, f_offset; /* Hz, integral, as for pcal_plan_create     */
@@ -341,6 +341,74 @@ int pcal_batch_get_stats(const pcal_batch* batch, pcal_stats* out);
  */
 int pcal_batch_autotune(pcal_batch* batch, const void* const* samples, const int64_t* n, void* stream,
                         pcal_schedule* chosen);
+
+/*
+ * ---- Serving: continuous batching of live streams ----------------------------
+ *
+ * A server holds up to max_streams live streams (2-bit or int8, each with its
+ * own fs, f_comb, f_offset, N).  A stream is admitted when its device memory
+ * -- bins, rotator table, results and a ring of ring_s seconds of samples --
+ * fits in what remains of hbm_budget_bytes (one device allocation the server
+ * owns); otherwise it is queued and admitted as closed streams return memory.
+ * Clients submit chunks of host samples; a scheduler thread folds every
+ * stream's pending samples with one persistent launch (the batched fold),
+ * finalizes each stream once period_s seconds of its samples are folded
+ * (Sec. 2), and publishes the results with their latency: from the return of
+ * the submit that brought a period's last sample to the results on the host.
+ * Work submitted while the GPU is busy joins the next launch (several are in
+ * flight).  The paper has no counterpart; serving is an interface choice of
+ * this library.  All calls are thread-safe; one client thread per stream.
+ */
+typedef struct {
+    int64_t hbm_budget_bytes; /* device memory for all streams                  */
+    int max_streams;          /* streams admitted at once, at most              */
+    double period_s;          /* integration period (fs*period_s samples, a multiple of 4) */
+    double ring_s;            /* device ring per stream, seconds of samples     */
+} pcal_server_config;
+
+typedef struct {
+    int32_t stream, n_tones;
+    int64_t period;           /* 0, 1, 2, ... for this stream                   */
+    int64_t n_samples;        /* samples in the period                          */
+    double td_s, sigma_td_s;  /* delay and its 1-sigma                          */
+    double latency_s;         /* last sample submitted -> results on the host  */
+} pcal_server_result;
+
+typedef struct {
+    int64_t admitted, queued, active, periods, samples, launches, bytes_h2d;
+    int64_t hbm_in_use, hbm_budget;
+    double p50_latency_s, p99_latency_s, max_latency_s;
+} pcal_server_stats;
+
+typedef struct pcal_server pcal_server;
+
+/* Device bytes a stream takes from the budget (host only, no CUDA call). */
+int pcal_server_stream_bytes(const pcal_server_config* config, const pcal_channel_desc* desc, int64_t* out);
+/* Create a server on the current device (allocates the whole budget, starts the scheduler thread). */
+int pcal_server_create(const pcal_server_config* config, pcal_server** out);
+/* Stop the scheduler after the work in flight; free everything.  Unfinished periods are dropped. */
+int pcal_server_destroy(pcal_server* server);
+/* Open a stream: validated as pcal_batch_create's channels; PCAL_ENOMEM if it could never fit the
+ * budget.  *stream_id is valid at once; the stream is admitted now or later (queued). */
+int pcal_server_open(pcal_server* server, const pcal_channel_desc* desc, int* stream_id);
+/* Copy n samples (HOST memory, pinned for speed; n a multiple of 4 for 2-bit, at most the ring)
+ * into the stream's device ring.  Blocks while the stream is queued or its ring is full; returns
+ * when the copy is done (the host buffer may then be reused). */
+int pcal_server_submit(pcal_server* server, int stream_id, const void* host_samples, int64_t n);
+/* One chunk for each of `count` distinct streams, copied together. */
+int pcal_server_submit_many(pcal_server* server, int count, const int* stream_ids, const void* const* host_samples,
+                            const int64_t* n);
+/* Close a stream: its submitted samples are still folded, a partial period is dropped, then its
+ * memory returns to the budget. */
+int pcal_server_close(pcal_server* server, int stream_id);
+/* Next published result: 1 and *out (and the 2*n_tones phasors, re/im interleaved, into phasors
+ * when not NULL; max_tones is its capacity in tones), or 0 when none arrived within timeout_s. */
+int pcal_server_poll(pcal_server* server, pcal_server_result* out, double* phasors, int max_tones,
+                     double timeout_s);
+/* Wait until every submitted sample is folded and every closed stream released. */
+int pcal_server_drain(pcal_server* server, double timeout_s);
+/* Counters and latency percentiles over all published periods. */
+int pcal_server_get_stats(pcal_server* server, pcal_server_stats* out);
 
 /* Static name of a status code. */
 const char* pcal_strerror(int code);

@@ -67,7 +67,29 @@ class Schedule(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-PCAL_MAX_BATCH, PCAL_BATCH_MAX_N = 4096, 256
+PCAL_MAX_BATCH, PCAL_BATCH_MAX_N = 4096, 1024
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_streams", ctypes.c_int), ("period_s", ctypes.c_double),
+                ("ring_s", ctypes.c_double)]
+
+
+class ServerResult(ctypes.Structure):
+    _fields_ = [("stream", ctypes.c_int32), ("n_tones", ctypes.c_int32), ("period", ctypes.c_int64),
+                ("n_samples", ctypes.c_int64), ("td_s", ctypes.c_double), ("sigma_td_s", ctypes.c_double),
+                ("latency_s", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("admitted", ctypes.c_int64), ("queued", ctypes.c_int64), ("active", ctypes.c_int64),
+                ("periods", ctypes.c_int64), ("samples", ctypes.c_int64), ("launches", ctypes.c_int64),
+                ("bytes_h2d", ctypes.c_int64), ("hbm_in_use", ctypes.c_int64), ("hbm_budget", ctypes.c_int64),
+                ("p50_latency_s", ctypes.c_double), ("p99_latency_s", ctypes.c_double),
+                ("max_latency_s", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class PcalError(RuntimeError):
@@ -121,6 +143,16 @@ def load(path: str | None = None):
         "pcal_batch_get_bins": ([vp, ci, vp], ci),
         "pcal_batch_get_stats": ([vp, P(Stats)], ci),
         "pcal_batch_autotune": ([vp, P(vp), P(i64), vp, P(Schedule)], ci),
+        "pcal_server_stream_bytes": ([P(ServerConfig), P(ChannelDesc), P(i64)], ci),
+        "pcal_server_create": ([P(ServerConfig), P(vp)], ci),
+        "pcal_server_destroy": ([vp], ci),
+        "pcal_server_open": ([vp, P(ChannelDesc), P(ci)], ci),
+        "pcal_server_submit": ([vp, ci, vp, i64], ci),
+        "pcal_server_submit_many": ([vp, ci, P(ci), P(vp), P(i64)], ci),
+        "pcal_server_close": ([vp, ci], ci),
+        "pcal_server_poll": ([vp, P(ServerResult), vp, ci, dbl], ci),
+        "pcal_server_drain": ([vp, dbl], ci),
+        "pcal_server_get_stats": ([vp, P(ServerStats)], ci),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -482,3 +514,86 @@ class Batch:
 
     def autotune(self, samples, n, stream=None) -> dict:
         return pcal_batch_autotune(self.handle, samples, n, stream).as_dict()
+
+
+# ---- serving --------------------------------------------------------------------------
+
+
+def pcal_server_stream_bytes(fs, f_comb, f_offset, fmt, period_s=1.0, ring_s=0.1, N=None) -> int:
+    cfg = ServerConfig(1, 1, float(period_s), float(ring_s))
+    d = ChannelDesc(float(fs), float(f_comb), float(f_offset), int(N if N is not None else round(fs / f_comb)),
+                    FORMATS[fmt] if isinstance(fmt, str) else int(fmt))
+    out = ctypes.c_int64()
+    _check(load().pcal_server_stream_bytes(ctypes.byref(cfg), ctypes.byref(d), ctypes.byref(out)),
+           "pcal_server_stream_bytes")
+    return out.value
+
+
+class Server:
+    """Live streams folded by continuous batching (see pcal_server_* in pcal.h)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_streams: int, period_s: float = 1.0, ring_s: float = 0.1):
+        cfg = ServerConfig(int(hbm_budget_bytes), int(max_streams), float(period_s), float(ring_s))
+        h = ctypes.c_void_p()
+        _check(load().pcal_server_create(ctypes.byref(cfg), ctypes.byref(h)), "pcal_server_create")
+        self.handle = h.value
+        self.n_tones = {}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(load().pcal_server_destroy(self.handle), "pcal_server_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def open(self, fs, f_comb, f_offset, fmt, N=None) -> int:
+        d = ChannelDesc(float(fs), float(f_comb), float(f_offset), int(N if N is not None else round(fs / f_comb)),
+                        FORMATS[fmt] if isinstance(fmt, str) else int(fmt))
+        sid = ctypes.c_int()
+        _check(load().pcal_server_open(self.handle, ctypes.byref(d), ctypes.byref(sid)), "pcal_server_open")
+        self.n_tones[sid.value] = d.N
+        return sid.value
+
+    def submit(self, stream: int, host: np.ndarray, n: int):
+        _check(load().pcal_server_submit(self.handle, int(stream), host.ctypes.data, int(n)), "pcal_server_submit")
+
+    def submit_many(self, streams, hosts, ns):
+        k = len(streams)
+        ids = (ctypes.c_int * k)(*[int(x) for x in streams])
+        ptrs = (ctypes.c_void_p * k)(*[h.ctypes.data for h in hosts])
+        nn = (ctypes.c_int64 * k)(*[int(x) for x in ns])
+        _check(load().pcal_server_submit_many(self.handle, k, ids, ctypes.cast(ptrs, ctypes.POINTER(ctypes.c_void_p)),
+                                              nn), "pcal_server_submit_many")
+
+    def close_stream(self, stream: int):
+        _check(load().pcal_server_close(self.handle, int(stream)), "pcal_server_close")
+
+    def poll(self, timeout_s: float = 0.0, max_tones: int = PCAL_BATCH_MAX_N):
+        r = ServerResult()
+        ph = np.empty(2 * max_tones)
+        rc = load().pcal_server_poll(self.handle, ctypes.byref(r), ph.ctypes.data, int(max_tones), float(timeout_s))
+        if rc < 0:
+            raise PcalError(rc, "pcal_server_poll")
+        if rc == 0:
+            return None
+        n = r.n_tones
+        return {"stream": r.stream, "period": r.period, "n_samples": r.n_samples, "td": r.td_s,
+                "sigma_td": r.sigma_td_s, "latency_s": r.latency_s, "phasors": ph[0:2 * n:2] + 1j * ph[1:2 * n:2]}
+
+    def drain(self, timeout_s: float = 60.0):
+        _check(load().pcal_server_drain(self.handle, float(timeout_s)), "pcal_server_drain")
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(load().pcal_server_get_stats(self.handle, ctypes.byref(st)), "pcal_server_get_stats")
+        return st.as_dict()

@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) batch_fold_kernel(const BatchFol
         Acc2 acc2;
         int s8[4] = {0, 0, 0, 0};
         if (producer) {
-            tensormap_acquire(&a.maps[seg.ch]);
+            tensormap_acquire(&a.maps[seg.map]);
             int run = 0, next = -1;
             bool ok = true;
             for (;;) {
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) batch_fold_kernel(const BatchFol
                 const int st = pj % a.stages;
                 s_hdr[st] = 0;
                 mbar_arrive_expect_tx(&full[st], (uint32_t)seg.tx_bytes);
-                tma_load_2d(smem + (size_t)st * a.stage_stride, &a.maps[seg.ch], seg.col0,
+                tma_load_2d(smem + (size_t)st * a.stage_stride, &a.maps[seg.map], seg.col0,
                             (int)(pending - seg.box_start) * a.box_rows, &full[st]);
                 s_last_fill[st] = pj;
                 s_fill_open[st] = 1;
@@ -468,22 +468,6 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // ---- host side ---------------------------------------------------------------------
 
-// Launch shape of the persistent fold for one schedule (host only).
-struct BatchShape {
-    int wpr, replicas, box_rows, stages, merge_stride, threads, grid, run_boxes;
-    uint32_t stage_stride;
-    size_t smem;
-};
-
-// Device descriptors of one call: tensor maps, segments, pieces, samples
-// per channel.
-struct BatchCallDesc {
-    std::vector<uint8_t> blob;  // host image of the device buffer
-    size_t off_maps, off_segs, off_pieces, off_n;
-    int n_segs, n_pieces;
-    long long total_boxes;
-};
-
 struct BatchGraph {
     std::vector<const void*> ptrs;
     std::vector<int64_t> n;
@@ -502,6 +486,7 @@ struct pcal_batch {
     void* d_pool;
     std::vector<int64_t> n_abs, period_start;  // host mirrors of the device indices
     int cw_max;
+    int max_n;  // largest N of the channels
     pcal_schedule sched;
     // descriptor ring for eager calls
     void* h_slot[kSlots];
@@ -517,19 +502,16 @@ struct pcal_batch {
     pcal_stats stats;
 };
 
-namespace {
-
-int shape_for(const pcal_batch* b, BatchShape* s) {
-    const pcal_schedule& sc = b->sched;
+int batch_shape(const pcal_schedule& sc, int cw_max, int num_sms, BatchShape* s) {
     BatchShape z{};
     z.box_rows = sc.box_rows;
-    z.wpr = (b->cw_max + 31) / 32;
+    z.wpr = (cw_max + 31) / 32;
     int r_max = (kMaxBlock / 32 - 1) / z.wpr;
     if (r_max > 8) r_max = 8;
     if (r_max < 1) r_max = 1;
-    const size_t stage = (size_t)z.box_rows * b->cw_max * 4;
+    const size_t stage = (size_t)z.box_rows * cw_max * 4;
     z.stage_stride = (uint32_t)align_up(stage, 1024);
-    z.merge_stride = (b->cw_max + 31) / 32 * 32 + 2;
+    z.merge_stride = (cw_max + 31) / 32 * 32 + 2;
     z.replicas = 0;
     for (int rr = r_max; rr >= 1 && z.replicas == 0; --rr) {
         int st = (int)((kSmemBudget - 1024) / z.stage_stride);
@@ -537,7 +519,7 @@ int shape_for(const pcal_batch* b, BatchShape* s) {
         if (st > 8) st = 8;
         st = st / rr * rr;
         if (st < 3 || st < rr) continue;
-        const size_t need = std::max((size_t)128 * rr * b->cw_max + (size_t)128 * z.merge_stride,
+        const size_t need = std::max((size_t)128 * rr * cw_max + (size_t)128 * z.merge_stride,
                                      (size_t)16 * z.merge_stride);
         if (need > (size_t)st * z.stage_stride) continue;
         z.replicas = rr;
@@ -546,29 +528,30 @@ int shape_for(const pcal_batch* b, BatchShape* s) {
     if (z.replicas == 0) return -1;
     z.threads = (z.wpr * z.replicas + 1) * 32;
     z.smem = (size_t)z.stages * z.stage_stride + 16 * (size_t)z.stages;
-    z.grid = sc.ctas > 0 ? sc.ctas : b->num_sms;
+    z.grid = sc.ctas > 0 ? sc.ctas : num_sms;
     z.run_boxes = kRunRows / z.box_rows;
+    z.static_pct = sc.static_pct;
+    z.min_chunk = sc.min_chunk > 0 ? sc.min_chunk : 1;
     *s = z;
     return 0;
 }
 
-// Build the descriptors of one call (host side; tensor maps encoded here).
-int build_call(pcal_batch* b, const void* const* samples, const int64_t* n, const BatchShape& sh,
-               BatchCallDesc* out) {
+int batch_build(const BatchChan* h_ch, int n_ch, const std::vector<BatchRegion>& regions, const BatchShape& sh,
+                const std::vector<int>& fin_list, BatchCallDesc* out) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
     if (!enc) return PCAL_ECUDA;
-    std::vector<CUtensorMap> maps(b->n);
+    std::vector<CUtensorMap> maps;
     std::vector<BatchSeg> segs;
     std::vector<BatchPiece> pieces;
-    std::vector<long long> ncall(b->n);
-    memset(maps.data(), 0, sizeof(CUtensorMap) * maps.size());
+    std::vector<long long> ncall(n_ch, 0);
     long long total = 0;
-    for (int c = 0; c < b->n; ++c) {
-        const BatchChan& C = b->h_ch[c];
-        const int64_t nc = n[c];
-        ncall[c] = nc;
+    for (const BatchRegion& rg : regions) {
+        if (rg.ch < 0 || rg.ch >= n_ch || rg.n < 0) return PCAL_EINVAL;
+        const BatchChan& C = h_ch[rg.ch];
+        const int64_t nc = rg.n;
+        ncall[rg.ch] += nc;
         if (nc == 0) continue;
-        const uint8_t* p = static_cast<const uint8_t*>(samples[c]);
+        const uint8_t* p = rg.ptr;
         const int spb = C.fmt == PCAL_2BIT ? 4 : 1;  // samples per byte
         const int64_t nbytes = nc / spb;
         int64_t head_bytes = (int64_t)((16 - (reinterpret_cast<uintptr_t>(p) & 15)) & 15);
@@ -576,34 +559,39 @@ int build_call(pcal_batch* b, const void* const* samples, const int64_t* n, cons
         const int64_t row_bytes = C.row_samples / spb;
         const int64_t rows = (nbytes - head_bytes) / row_bytes;
         if (rows < 1) {
-            pieces.push_back(BatchPiece{p, nc, 0, c, 0});
+            pieces.push_back(BatchPiece{p, nc, rg.off, rg.ch, 0});
             continue;
         }
-        if (head_bytes > 0) pieces.push_back(BatchPiece{p, head_bytes * spb, 0, c, 0});
+        if (head_bytes > 0) pieces.push_back(BatchPiece{p, head_bytes * spb, rg.off, rg.ch, 0});
         const uint8_t* body = p + head_bytes;
+        CUtensorMap map;
+        memset(&map, 0, sizeof(map));
         cuuint64_t dims[2] = {(cuuint64_t)C.cols_total, (cuuint64_t)rows};
         cuuint64_t strides[1] = {(cuuint64_t)row_bytes};
         cuuint32_t box[2] = {(cuuint32_t)C.col_width, (cuuint32_t)sh.box_rows};
         cuuint32_t estr[2] = {1, 1};
-        CUresult r = enc(&maps[c], CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<uint8_t*>(body), dims, strides, box,
+        CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<uint8_t*>(body), dims, strides, box,
                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return PCAL_EINVAL;
+        const int map_index = (int)maps.size();
+        maps.push_back(map);
         const int nbox = (int)((rows + sh.box_rows - 1) / sh.box_rows);
         for (int gc = 0; gc < C.col_groups; ++gc) {
-            BatchSeg s{};
-            s.box_start = total;
-            s.n_boxes = nbox;
-            s.ch = c;
-            s.col0 = gc * C.col_width;
-            s.tx_bytes = sh.box_rows * C.col_width * 4;
-            s.head = head_bytes * spb;
-            segs.push_back(s);
+            BatchSeg sg{};
+            sg.box_start = total;
+            sg.n_boxes = nbox;
+            sg.ch = rg.ch;
+            sg.map = map_index;
+            sg.col0 = gc * C.col_width;
+            sg.tx_bytes = sh.box_rows * C.col_width * 4;
+            sg.head = rg.off + head_bytes * spb;
+            segs.push_back(sg);
             total += nbox;
         }
         const int64_t tail_byte = head_bytes + rows * row_bytes;
         if (tail_byte < nbytes)
-            pieces.push_back(BatchPiece{p + tail_byte, (nbytes - tail_byte) * spb, tail_byte * spb, c, 0});
+            pieces.push_back(BatchPiece{p + tail_byte, (nbytes - tail_byte) * spb, rg.off + tail_byte * spb, rg.ch, 0});
     }
     if (total >= (1LL << 31)) return PCAL_ETOOLARGE;
     BatchCallDesc d;
@@ -611,36 +599,40 @@ int build_call(pcal_batch* b, const void* const* samples, const int64_t* n, cons
     d.off_segs = align_up(sizeof(CUtensorMap) * maps.size(), 128);
     d.off_pieces = align_up(d.off_segs + sizeof(BatchSeg) * segs.size(), 128);
     d.off_n = align_up(d.off_pieces + sizeof(BatchPiece) * pieces.size(), 128);
-    const size_t bytes = align_up(d.off_n + sizeof(long long) * ncall.size(), 128);
+    d.off_list = align_up(d.off_n + sizeof(long long) * ncall.size(), 128);
+    const size_t bytes = align_up(d.off_list + sizeof(int) * fin_list.size(), 128);
     d.blob.assign(bytes, 0);
-    memcpy(d.blob.data() + d.off_maps, maps.data(), sizeof(CUtensorMap) * maps.size());
+    if (!maps.empty()) memcpy(d.blob.data() + d.off_maps, maps.data(), sizeof(CUtensorMap) * maps.size());
     if (!segs.empty()) memcpy(d.blob.data() + d.off_segs, segs.data(), sizeof(BatchSeg) * segs.size());
     if (!pieces.empty()) memcpy(d.blob.data() + d.off_pieces, pieces.data(), sizeof(BatchPiece) * pieces.size());
     memcpy(d.blob.data() + d.off_n, ncall.data(), sizeof(long long) * ncall.size());
+    if (!fin_list.empty()) memcpy(d.blob.data() + d.off_list, fin_list.data(), sizeof(int) * fin_list.size());
     d.n_segs = (int)segs.size();
     d.n_pieces = (int)pieces.size();
+    d.n_list = (int)fin_list.size();
     d.total_boxes = total;
     *out = std::move(d);
     return PCAL_OK;
 }
 
-// Launch the kernels of one call whose descriptors are at d_desc.
-cudaError_t launch_call(pcal_batch* b, const BatchCallDesc& d, void* d_desc, unsigned long long* d_ctr,
-                        const BatchShape& sh, cudaStream_t s) {
+cudaError_t batch_launch_fold(const BatchCallDesc& d, void* d_desc, BatchChan* d_ch, int n_ch,
+                              unsigned long long* d_ctr, const BatchShape& sh, unsigned int* d_err, cudaStream_t s,
+                              int* launches) {
     uint8_t* base = static_cast<uint8_t*>(d_desc);
     cudaError_t e = cudaSuccess;
+    *launches = 0;
     if (d.total_boxes > 0) {
         BatchFoldArgs a{};
         a.maps = reinterpret_cast<const CUtensorMap*>(base + d.off_maps);
         a.segs = reinterpret_cast<const BatchSeg*>(base + d.off_segs);
         a.n_segs = d.n_segs;
-        a.ch = b->d_ch;
+        a.ch = d_ch;
         a.total_boxes = d.total_boxes;
         long long grid = sh.grid;
         if (grid > d.total_boxes) grid = d.total_boxes;
-        a.static_boxes = (long long)((double)b->sched.static_pct / 100.0 * (double)d.total_boxes / (double)grid);
+        a.static_boxes = (long long)((double)sh.static_pct / 100.0 * (double)d.total_boxes / (double)grid);
         a.pool_start = a.static_boxes * grid;
-        a.min_chunk = b->sched.min_chunk > 0 ? b->sched.min_chunk : 1;
+        a.min_chunk = sh.min_chunk;
         a.ctr = d_ctr;
         a.box_rows = sh.box_rows;
         a.stages = sh.stages;
@@ -649,25 +641,112 @@ cudaError_t launch_call(pcal_batch* b, const BatchCallDesc& d, void* d_desc, uns
         a.merge_stride = sh.merge_stride;
         a.run_boxes = sh.run_boxes;
         a.stage_stride = sh.stage_stride;
-        a.err = b->d_err;
+        a.err = d_err;
         e = cudaMemsetAsync(d_ctr, 0, sizeof(unsigned long long), s);
         if (e != cudaSuccess) return e;
         batch_fold_kernel<<<(unsigned)grid, sh.threads, sh.smem, s>>>(a);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        b->stats.kernel_launches += 1;
-        b->stats.bulk_launches += 1;
+        *launches += 1;
     }
     if (d.n_pieces > 0) {
         batch_ragged_kernel<<<dim3(32, (unsigned)d.n_pieces), 256, 0, s>>>(
-            reinterpret_cast<const BatchPiece*>(base + d.off_pieces), b->d_ch);
+            reinterpret_cast<const BatchPiece*>(base + d.off_pieces), d_ch);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        b->stats.kernel_launches += 1;
+        *launches += 1;
     }
-    batch_advance_kernel<<<1, 128, 0, s>>>(b->d_ch, reinterpret_cast<const long long*>(base + d.off_n), b->n);
-    b->stats.kernel_launches += 1;
+    batch_advance_kernel<<<1, 128, 0, s>>>(d_ch, reinterpret_cast<const long long*>(base + d.off_n), n_ch);
+    *launches += 1;
     return cudaGetLastError();
+}
+
+cudaError_t batch_prepare_fold() {
+    return cudaFuncSetAttribute(batch_fold_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget);
+}
+
+cudaError_t batch_launch_tables(BatchChan& C, const pcal_geometry& g, cudaStream_t s) {
+    int grid = (int)((g.L + 255) / 256);
+    if (grid > 1024) grid = 1024;
+    batch_tables_kernel<<<grid, 256, 0, s>>>(const_cast<double2*>(C.tw), g.L, const_cast<float2*>(C.twN), g.N,
+                                             g.step_comb);
+    return cudaGetLastError();
+}
+
+// Fill the constant part of a channel's device record (pointers excluded).
+void batch_fill_chan(BatchChan& C, const pcal_geometry& g, double f_comb, int col_cap) {
+    memset(static_cast<void*>(&C), 0, sizeof(C));
+    C.fmt = g.format;
+    C.spw = g.samples_per_byte_x4;
+    C.N = (int)g.N;
+    C.L = (int)g.L;
+    C.so = g.step_offset;
+    C.row_samples = g.row_samples;
+    C.cols_total = (int)(g.row_samples / C.spw);
+    int gc = (C.cols_total + col_cap - 1) / col_cap;
+    int cw = (C.cols_total + gc - 1) / gc;
+    cw = (cw + 7) / 8 * 8;
+    if (cw > col_cap) cw = col_cap;
+    C.col_groups = (C.cols_total + cw - 1) / cw;
+    C.col_width = cw;
+    const double lv[4] = {-3.3359, -1.0, 1.0, 3.3359};
+    C.lev0 = g.format == PCAL_2BIT ? lv[0] : 0.0;
+    C.c_l = g.format == PCAL_2BIT ? lv[1] - lv[0] : 0.0;
+    C.c_h = g.format == PCAL_2BIT ? lv[2] - lv[0] : 0.0;
+    C.c_hl = g.format == PCAL_2BIT ? lv[3] - lv[2] - lv[1] + lv[0] : 0.0;
+    C.two_pi_fc = 6.283185307179586476925 * f_comb;
+}
+
+// Device bytes of one channel's bins, tables and results (each part 256-byte aligned).
+size_t batch_chan_bytes(const pcal_geometry& g) {
+    const size_t L = (size_t)g.L, N = (size_t)g.N;
+    size_t n = 0;
+    if (g.format == PCAL_2BIT) n += align_up(8 * L, 256) + align_up(24 * L, 256);
+    if (g.format == PCAL_I8) n += align_up(8 * L, 256);
+    n += align_up(16 * L, 256) + align_up(8 * N, 256) + align_up(8 * (5 * N + 3), 256);
+    return n;
+}
+
+// Point a channel's record into `base` (batch_chan_bytes(g) bytes, 256-aligned).
+void batch_place_chan(BatchChan& C, const pcal_geometry& g, uint8_t* base) {
+    const size_t L = (size_t)g.L, N = (size_t)g.N;
+    size_t o = 0;
+    if (g.format == PCAL_2BIT) {
+        C.zero2 = reinterpret_cast<unsigned long long*>(base + o);
+        o += align_up(8 * L, 256);
+        C.wide2 = reinterpret_cast<unsigned long long*>(base + o);
+        o += align_up(24 * L, 256);
+    }
+    if (g.format == PCAL_I8) {
+        C.acc8 = reinterpret_cast<long long*>(base + o);
+        o += align_up(8 * L, 256);
+    }
+    C.tw = reinterpret_cast<double2*>(base + o);
+    o += align_up(16 * L, 256);
+    C.twN = reinterpret_cast<float2*>(base + o);
+    o += align_up(8 * N, 256);
+    C.res = reinterpret_cast<double*>(base + o);
+}
+
+namespace {
+
+int shape_for(const pcal_batch* b, BatchShape* s) { return batch_shape(b->sched, b->cw_max, b->num_sms, s); }
+
+int build_call(pcal_batch* b, const void* const* samples, const int64_t* n, const BatchShape& sh,
+               BatchCallDesc* out) {
+    std::vector<BatchRegion> regions;
+    for (int c = 0; c < b->n; ++c)
+        regions.push_back(BatchRegion{c, static_cast<const uint8_t*>(samples[c]), n[c], 0});
+    return batch_build(b->h_ch.data(), b->n, regions, sh, std::vector<int>(), out);
+}
+
+cudaError_t launch_call(pcal_batch* b, const BatchCallDesc& d, void* d_desc, unsigned long long* d_ctr,
+                        const BatchShape& sh, cudaStream_t s) {
+    int launches = 0;
+    const cudaError_t e = batch_launch_fold(d, d_desc, b->d_ch, b->n, d_ctr, sh, b->d_err, s, &launches);
+    b->stats.kernel_launches += launches;
+    if (d.total_boxes > 0) b->stats.bulk_launches += 1;
+    return e;
 }
 
 }  // namespace
@@ -684,8 +763,7 @@ extern "C" int pcal_batch_create(const pcal_channel_desc* channels, int n_channe
     b->period_start.assign(n_channels, 0);
     b->sched = pcal_schedule{0, 32, 0, 90, 4, 224};
     size_t pool = 0;
-    std::vector<size_t> off_zero(n_channels), off_wide(n_channels), off_acc8(n_channels), off_tw(n_channels),
-        off_twN(n_channels), off_res(n_channels);
+    std::vector<size_t> off(n_channels);
     for (int c = 0; c < n_channels; ++c) {
         const pcal_channel_desc& d = channels[c];
         if (d.sample_format != PCAL_2BIT && d.sample_format != PCAL_I8) {
@@ -701,19 +779,8 @@ extern "C" int pcal_batch_create(const pcal_channel_desc* channels, int n_channe
             delete b;
             return PCAL_ETOOLARGE;
         }
-        const int64_t L = b->g[c].L, N = b->g[c].N;
-        off_zero[c] = pool;
-        pool = align_up(pool + (d.sample_format == PCAL_2BIT ? 8 * L : 0), 256);
-        off_wide[c] = pool;
-        pool = align_up(pool + (d.sample_format == PCAL_2BIT ? 24 * L : 0), 256);
-        off_acc8[c] = pool;
-        pool = align_up(pool + (d.sample_format == PCAL_I8 ? 8 * L : 0), 256);
-        off_tw[c] = pool;
-        pool = align_up(pool + 16 * L, 256);
-        off_twN[c] = pool;
-        pool = align_up(pool + 8 * N, 256);
-        off_res[c] = pool;
-        pool = align_up(pool + 8 * (5 * N + 3), 256);
+        off[c] = pool;
+        pool += batch_chan_bytes(b->g[c]);
     }
     cudaError_t e = cudaGetDevice(&b->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
@@ -726,46 +793,17 @@ extern "C" int pcal_batch_create(const pcal_channel_desc* channels, int n_channe
     e = cudaMemset(b->d_pool, 0, pool);
     uint8_t* base = static_cast<uint8_t*>(b->d_pool);
     b->cw_max = 8;
+    b->max_n = 1;
     for (int c = 0; c < n_channels && e == cudaSuccess; ++c) {
-        const pcal_geometry& g = b->g[c];
-        const pcal_channel_desc& d = channels[c];
         BatchChan& C = b->h_ch[c];
-        memset(static_cast<void*>(&C), 0, sizeof(C));
-        C.fmt = g.format;
-        C.spw = g.samples_per_byte_x4;
-        C.N = (int)g.N;
-        C.L = (int)g.L;
-        C.so = g.step_offset;
-        C.row_samples = g.row_samples;
-        C.cols_total = (int)(g.row_samples / C.spw);
-        int gc = (C.cols_total + 223) / 224;
-        int cw = (C.cols_total + gc - 1) / gc;
-        cw = (cw + 7) / 8 * 8;
-        if (cw > 224) cw = 224;
-        C.col_groups = (C.cols_total + cw - 1) / cw;
-        C.col_width = cw;
-        if (cw > b->cw_max) b->cw_max = cw;
-        C.zero2 = g.format == PCAL_2BIT ? reinterpret_cast<unsigned long long*>(base + off_zero[c]) : nullptr;
-        C.wide2 = g.format == PCAL_2BIT ? reinterpret_cast<unsigned long long*>(base + off_wide[c]) : nullptr;
-        C.acc8 = g.format == PCAL_I8 ? reinterpret_cast<long long*>(base + off_acc8[c]) : nullptr;
-        C.tw = reinterpret_cast<double2*>(base + off_tw[c]);
-        C.twN = reinterpret_cast<float2*>(base + off_twN[c]);
-        C.res = reinterpret_cast<double*>(base + off_res[c]);
-        const double lv[4] = {-3.3359, -1.0, 1.0, 3.3359};
-        C.lev0 = g.format == PCAL_2BIT ? lv[0] : 0.0;
-        C.c_l = g.format == PCAL_2BIT ? lv[1] - lv[0] : 0.0;
-        C.c_h = g.format == PCAL_2BIT ? lv[2] - lv[0] : 0.0;
-        C.c_hl = g.format == PCAL_2BIT ? lv[3] - lv[2] - lv[1] + lv[0] : 0.0;
-        C.two_pi_fc = 6.283185307179586476925 * d.f_comb;
-        int grid = (int)((g.L + 255) / 256);
-        if (grid > 1024) grid = 1024;
-        batch_tables_kernel<<<grid, 256>>>(const_cast<double2*>(C.tw), g.L, const_cast<float2*>(C.twN), g.N,
-                                           g.step_comb);
-        e = cudaGetLastError();
+        batch_fill_chan(C, b->g[c], channels[c].f_comb, b->sched.col_cap);
+        batch_place_chan(C, b->g[c], base + off[c]);
+        if (C.col_width > b->cw_max) b->cw_max = C.col_width;
+        if (C.N > b->max_n) b->max_n = C.N;
+        e = batch_launch_tables(C, b->g[c], nullptr);
     }
     // function attributes now: a stream capture of a step must not set them
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(batch_fold_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget);
+    if (e == cudaSuccess) e = batch_prepare_fold();
     if (e == cudaSuccess) e = prepare_batch_finalize();
     if (e == cudaSuccess) e = cudaMalloc(&b->d_ch, sizeof(BatchChan) * n_channels);
     if (e == cudaSuccess)
@@ -893,7 +931,7 @@ extern "C" int pcal_batch_accumulate(pcal_batch* b, const void* const* samples, 
 extern "C" int pcal_batch_finalize_device(pcal_batch* b, void* stream) {
     if (!b) return PCAL_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t e = launch_batch_finalize(b->d_ch, b->n, s);
+    cudaError_t e = launch_batch_finalize(b->d_ch, b->n, b->max_n, nullptr, s);
     if (e != cudaSuccess) return PCAL_ECUDA;
     b->stats.kernel_launches += 1;
     b->last_stream = s;
@@ -938,7 +976,7 @@ extern "C" int pcal_batch_step_graph(pcal_batch* b, const void* const* samples, 
         if (e == cudaSuccess) {
             const pcal_stats keep = b->stats;
             cudaError_t el = launch_call(b, d, gr.d_desc, gr.d_ctr, sh, cap);
-            if (el == cudaSuccess) el = launch_batch_finalize(b->d_ch, b->n, cap);
+            if (el == cudaSuccess) el = launch_batch_finalize(b->d_ch, b->n, b->max_n, nullptr, cap);
             b->stats = keep;
             e = cudaStreamEndCapture(cap, &graph);
             if (el != cudaSuccess) e = el;

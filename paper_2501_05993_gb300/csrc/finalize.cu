@@ -431,9 +431,10 @@ __global__ void fin_fold_kernel(FinArgs a) {
 
 // ---- one-cluster finalize (N <= kClusterMaxN) ------------------------------
 
-constexpr int kClusterMaxN = 256;
+constexpr int kClusterMaxN = 256;       // single plans: the cluster path up to here
+constexpr int kClusterBigN = 1024;      // batches: the cluster path up to here (DFT spread over the cluster)
 constexpr int kClusterThreads = 256;
-constexpr size_t kClusterPadSmem = 28 * 1024;
+constexpr size_t kClusterPadSmem = 24 * 1024;
 constexpr int64_t kClusterMaxL = 32768;
 
 // Exclusive df prefix sum across the 32 lanes of a warp (fixed order).
@@ -463,16 +464,40 @@ __device__ __forceinline__ void warp_sums_df(df (&v)[K]) {
 // Shared memory of tone_products_warp: per tone the phase, the weight and
 // the unwrapped phase (df).
 struct WarpProductsSmem {
-    float psi[kClusterMaxN];
-    float w[kClusterMaxN];
-    float2 un[kClusterMaxN];
-    float2 out[2];  // td, sigma (df)
+    float2* un;   // [N] unwrapped phase (df)
+    float2* out;  // [2] td, sigma (df)
+    float* psi;   // [N]
+    float* w;     // [N]
 };
 
+// Dynamic shared memory of the cluster finalize for N tones.
+struct ClusterSmem {
+    float4* Pr;   // [N] this CTA's partial P (df re, df im)
+    float2* sP;   // [N] P
+    float2* sTw;  // [N] DFT twiddles
+    float2* sT;   // [N] tone phasors
+    WarpProductsSmem pm;
+};
+
+__host__ __device__ inline size_t cluster_smem_bytes(int64_t N) { return (size_t)N * 56 + 16; }
+
+__device__ inline ClusterSmem cluster_layout(uint8_t* base, int64_t N) {
+    ClusterSmem m;
+    m.Pr = reinterpret_cast<float4*>(base);
+    m.sP = reinterpret_cast<float2*>(base + 16 * N);
+    m.sTw = m.sP + N;
+    m.sT = m.sTw + N;
+    m.pm.un = m.sT + N;
+    m.pm.out = m.pm.un + N;
+    m.pm.psi = reinterpret_cast<float*>(m.pm.out + 2);
+    m.pm.w = m.pm.psi + N;
+    return m;
+}
+
 // The products of tone_products, by one warp with no block barrier: lane l
-// takes the contiguous tones [l*c, l*c + c), c = ceil(N/32) <= 8.  Loops over
-// a lane's tones are not unrolled, for the reason given at warp_sums_df.
-__device__ __noinline__ void tone_products_warp(const FinArgs& a, const float2* sT, WarpProductsSmem& m) {
+// takes the contiguous tones [l*c, l*c + c), c = ceil(N/32).  Loops over a
+// lane's tones are not unrolled, for the reason given at warp_sums_df.
+__device__ __noinline__ void tone_products_warp(const FinArgs& a, const float2* sT, const WarpProductsSmem& m) {
     const int N = (int)a.N;
     const int lane = threadIdx.x & 31;
     const int c = (N + 31) / 32;
@@ -563,6 +588,88 @@ __device__ void write_results_block(const FinArgs& a, const float2* sT, const Wa
     }
 }
 
+// Decode, rotate (FP64, Eq. 3) and fold residue b over m = m, m + step, ...
+// below m_end (bins k = b + m*N), clearing each bin; returns the FP64 sum.
+__device__ __forceinline__ double2 fold_residue(const FinArgs& a, int b, int m, int step, int m_end) {
+    double re = 0.0, im = 0.0;
+    if (m >= m_end) return make_double2(0.0, 0.0);
+    const int L = (int)a.L, N = (int)a.N;
+    int k = b + m * N;
+    int idx = (int)((a.so * k) % L);  // rotator index (f_offset/g * k) mod L
+    const int kstep = step * N;
+    const int istep = (int)((a.so * kstep) % L);
+    if (a.fmt == PCAL_2BIT && !a.spilled) {
+        // S = lev0*cnt + c_l*sum(l) + c_h*sum(h) + c_hl*sum(h AND l),
+        // cnt = q or q + 1; the fields are below 2^21
+        const double s_q = a.lev0 * (double)a.q, s_q1 = a.lev0 * (double)(a.q + 1);
+        const int a0 = (int)a.a0, rem = (int)a.rem;
+#pragma unroll 2
+        for (; m < m_end; m += step) {
+            const unsigned long long v = a.acc2[k];
+            const double2 w = a.tw[idx];
+            a.acc2[k] = 0;
+            int rr = k - a0;
+            if (rr < 0) rr += L;
+            const double S = fma(a.c_hl, (double)(int)((v >> 42) & PCAL_F21_MASK),
+                                 fma(a.c_h, (double)(int)((v >> 21) & PCAL_F21_MASK),
+                                     fma(a.c_l, (double)(int)(v & PCAL_F21_MASK), rr < rem ? s_q1 : s_q)));
+            re = fma(S, w.x, re);
+            im = fma(S, w.y, im);
+            k += kstep;
+            idx += istep;
+            if (idx >= L) idx -= L;
+        }
+    } else {
+#pragma unroll 1
+        for (; m < m_end; m += step) {
+            const double S = read_bin<false>(a, k);
+            const double2 w = a.tw[idx];
+            re = fma(S, w.x, re);
+            im = fma(S, w.y, im);
+            clear_bin(a, k);
+            k += kstep;
+            idx += istep;
+            if (idx >= L) idx -= L;
+        }
+    }
+    return make_double2(re, im);
+}
+
+// Tones [i0, i1) of the N-point DFT of sP in FP32 (g threads per tone,
+// combined by a fixed butterfly), written to dst[i] (shared memory of this
+// CTA or, through the cluster, of another).
+__device__ void dft_range(const float2* sP, const float2* sTw, int N, int i0, int i1, float2* dst) {
+    const int t = threadIdx.x;
+    const int ntone = i1 - i0;
+    int g = 1;
+    while (g < 32 && g * 2 * ntone <= (int)blockDim.x) g *= 2;
+    const int groups = blockDim.x / g;
+    const int gs = t % g;
+#pragma unroll 1
+    for (int base = 0; base < ntone; base += groups) {
+        const int i = i0 + base + t / g;
+        float sre = 0.f, sim = 0.f;
+        if (i < i1) {
+            int ix = (int)(((int64_t)i * gs) % N);
+            const int step = (int)(((int64_t)i * g) % N);
+#pragma unroll 4
+            for (int bb = gs; bb < N; bb += g) {
+                const float2 p = sP[bb];
+                const float2 w = sTw[ix];
+                sre = fmaf(p.x, w.x, fmaf(-p.y, w.y, sre));
+                sim = fmaf(p.x, w.y, fmaf(p.y, w.x, sim));
+                ix += step;
+                if (ix >= N) ix -= N;
+            }
+        }
+        for (int o = g / 2; o > 0; o >>= 1) {
+            sre += __shfl_xor_sync(0xffffffffu, sre, o);
+            sim += __shfl_xor_sync(0xffffffffu, sim, o);
+        }
+        if (i < i1 && gs == 0) dst[i] = make_float2(sre, sim);
+    }
+}
+
 // The whole finalize in one cluster of C CTAs.  Thread t of every CTA takes
 // residue b = t % N and every (blockDim/N)-th index m of its CTA's slice
 // [per*r/C, per*(r+1)/C) of m = 0..per-1 (per = L/N), i.e. bins k = b + m*N:
@@ -578,148 +685,114 @@ __device__ __forceinline__ bool cluster_finalize(const FinArgs& a) {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     __shared__ float4 part[kClusterThreads];  // per (lane, residue) df partials: re hi, re lo, im hi, im lo
-    __shared__ float4 Pr[kClusterMaxN];       // this CTA's partial P
-    __shared__ float2 sP[kClusterMaxN], sTw[kClusterMaxN], sT[kClusterMaxN];
-    __shared__ WarpProductsSmem pm;
+    extern __shared__ __align__(16) uint8_t dsm[];
     const int C = (int)cluster.num_blocks(), r = (int)cluster.block_rank();
     const int N = (int)a.N;
+    const ClusterSmem sm = cluster_layout(dsm, N);
+    float4* Pr = sm.Pr;
+    float2 *sP = sm.sP, *sTw = sm.sTw, *sT = sm.sT;
     const int t = threadIdx.x;
-    const int lanes = (int)blockDim.x / N;
-    const int b = t % N, ml = t / N;
-    if (r == 0)
+    // N > blockDim: one lane per residue, the residues in turns
+    const bool big = N > (int)blockDim.x;
+    const int lanes = big ? 1 : (int)blockDim.x / N;
+    if (r == 0 || N > kClusterMaxN)
         for (int i = t; i < N; i += blockDim.x) sTw[i] = a.twN[i];
     // L <= PCAL_MAX_L: bin and rotator indices fit 32 bits (so*k does not)
     const int L = (int)a.L;
-    const int64_t so = a.so;
     const int per = L / N;
-    double re = 0.0, im = 0.0;
-    if (ml < lanes) {
-        const int m1 = per * (r + 1) / C;
-        int m = per * r / C + ml;
-        if (m < m1) {
-            int k = b + m * N;
-            int idx = (int)((so * k) % L);  // rotator index (f_offset/g * k) mod L
-            const int kstep = lanes * N;
-            const int istep = (int)((so * kstep) % L);
-            if (a.fmt == PCAL_2BIT && !a.spilled) {
-                // S = lev0*cnt + c_l*sum(l) + c_h*sum(h) + c_hl*sum(h AND l),
-                // cnt = q or q + 1; the fields are below 2^21
-                const double s_q = a.lev0 * (double)a.q, s_q1 = a.lev0 * (double)(a.q + 1);
-                const int a0 = (int)a.a0, rem = (int)a.rem;
-#pragma unroll 2
-                for (; m < m1; m += lanes) {
-                    const unsigned long long v = a.acc2[k];
-                    const double2 w = a.tw[idx];
-                    a.acc2[k] = 0;
-                    int rr = k - a0;
-                    if (rr < 0) rr += L;
-                    const double S = fma(a.c_hl, (double)(int)((v >> 42) & PCAL_F21_MASK),
-                                         fma(a.c_h, (double)(int)((v >> 21) & PCAL_F21_MASK),
-                                             fma(a.c_l, (double)(int)(v & PCAL_F21_MASK), rr < rem ? s_q1 : s_q)));
-                    re = fma(S, w.x, re);
-                    im = fma(S, w.y, im);
-                    k += kstep;
-                    idx += istep;
-                    if (idx >= L) idx -= L;
-                }
-            } else {
-#pragma unroll 1
-                for (; m < m1; m += lanes) {
-                    const double S = read_bin<false>(a, k);
-                    const double2 w = a.tw[idx];
-                    re = fma(S, w.x, re);
-                    im = fma(S, w.y, im);
-                    clear_bin(a, k);
-                    k += kstep;
-                    idx += istep;
-                    if (idx >= L) idx -= L;
-                }
-            }
-        }
-        const df dre = df_of(re), dim = df_of(im);
-        part[t] = make_float4(dre.hi, dre.lo, dim.hi, dim.lo);
-    }
-    __syncthreads();
-    if (t < N) {
-        df sr{0.f, 0.f}, si{0.f, 0.f};
-#pragma unroll 1
-        for (int l = 0; l < lanes; ++l) {
-            const float4 v = part[l * N + t];
-            sr = pcal_df::add(sr, df{v.x, v.y});
-            si = pcal_df::add(si, df{v.z, v.w});
-        }
-        Pr[t] = make_float4(sr.hi, sr.lo, si.hi, si.lo);
-    }
-    cluster.sync();  // every CTA's partial P is complete
-    if (r == 0) {
-        // thread t: residue t % N, ranks g, g + G, ... (g = t / N, G groups);
-        // the loads are issued together, then added in rank order
-        const int G = lanes < C ? lanes : C;
-        const int g = t / N;
-        if (g < G) {
-            df sr{0.f, 0.f}, si{0.f, 0.f};
-#pragma unroll 1
-            for (int q0 = g; q0 < C; q0 += 4 * G) {
-                float4 v[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int q = q0 + u * G;
-                    v[u] = q < C ? *cluster.map_shared_rank(&Pr[t % N], q) : make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    sr = pcal_df::add(sr, df{v[u].x, v[u].y});
-                    si = pcal_df::add(si, df{v[u].z, v[u].w});
-                }
-            }
-            part[t] = make_float4(sr.hi, sr.lo, si.hi, si.lo);
+    const int m1 = per * (r + 1) / C;
+    if (!big) {
+        // thread t: residue t % N, every lanes-th m of this CTA's slice
+        const int b = t % N, ml = t / N;
+        if (ml < lanes) {
+            const double2 z = fold_residue(a, b, per * r / C + ml, lanes, m1);
+            const df dre = df_of(z.x), dim = df_of(z.y);
+            part[t] = make_float4(dre.hi, dre.lo, dim.hi, dim.lo);
         }
         __syncthreads();
         if (t < N) {
             df sr{0.f, 0.f}, si{0.f, 0.f};
 #pragma unroll 1
-            for (int gg = 0; gg < G; ++gg) {
-                const float4 v = part[gg * N + t];
+            for (int l = 0; l < lanes; ++l) {
+                const float4 v = part[l * N + t];
                 sr = pcal_df::add(sr, df{v.x, v.y});
                 si = pcal_df::add(si, df{v.z, v.w});
             }
-            sP[t] = make_float2(sr.hi + sr.lo, si.hi + si.lo);
+            Pr[t] = make_float4(sr.hi, sr.lo, si.hi, si.lo);
+        }
+    } else {
+        // one thread per residue, the residues in turns
+#pragma unroll 1
+        for (int b = t; b < N; b += blockDim.x) {
+            const double2 z = fold_residue(a, b, per * r / C, 1, m1);
+            const df dre = df_of(z.x), dim = df_of(z.y);
+            Pr[b] = make_float4(dre.hi, dre.lo, dim.hi, dim.lo);
         }
     }
-    cluster.sync();  // the other CTAs' shared memory is no longer read
-    if (r != 0) return false;
-    // N-point DFT in FP32 from shared memory: g threads per tone
-    int g = 1;
-    while (g < 32 && g * 2 * N <= (int)blockDim.x) g *= 2;
-    const int groups = blockDim.x / g;
-    const int gs = t % g;
+    cluster.sync();  // every CTA's partial P is complete
+    if (r == 0) {
+        // residue i: the C partials in rank order, loads issued in fours;
+        // G threads share a residue when N is small
+        const int G = big ? 1 : (lanes < C ? lanes : C);
+        const int g = big ? 0 : t / N;
+        if (g < G) {
 #pragma unroll 1
-    for (int base = 0; base < N; base += groups) {
-        const int i = base + t / g;
-        float sre = 0.f, sim = 0.f;
-        if (i < N) {
-            int ix = (i * gs) % N;
-            const int step = (i * g) % N;
-#pragma unroll 4
-            for (int bb = gs; bb < N; bb += g) {
-                const float2 p = sP[bb];
-                const float2 w = sTw[ix];
-                sre = fmaf(p.x, w.x, fmaf(-p.y, w.y, sre));
-                sim = fmaf(p.x, w.y, fmaf(p.y, w.x, sim));
-                ix += step;
-                if (ix >= N) ix -= N;
+            for (int i = big ? t : t % N; i < N; i += big ? blockDim.x : N) {
+                df sr{0.f, 0.f}, si{0.f, 0.f};
+#pragma unroll 1
+                for (int q0 = g; q0 < C; q0 += 4 * G) {
+                    float4 v[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int q = q0 + u * G;
+                        v[u] = q < C ? *cluster.map_shared_rank(&Pr[i], q) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        sr = pcal_df::add(sr, df{v[u].x, v[u].y});
+                        si = pcal_df::add(si, df{v[u].z, v[u].w});
+                    }
+                }
+                if (big)
+                    sP[i] = make_float2(sr.hi + sr.lo, si.hi + si.lo);
+                else
+                    part[t] = make_float4(sr.hi, sr.lo, si.hi, si.lo);
+                if (!big) break;
             }
         }
-        for (int o = g / 2; o > 0; o >>= 1) {
-            sre += __shfl_xor_sync(0xffffffffu, sre, o);
-            sim += __shfl_xor_sync(0xffffffffu, sim, o);
+        if (!big) {
+            __syncthreads();
+            if (t < N) {
+                df sr{0.f, 0.f}, si{0.f, 0.f};
+#pragma unroll 1
+                for (int gg = 0; gg < G; ++gg) {
+                    const float4 v = part[gg * N + t];
+                    sr = pcal_df::add(sr, df{v.x, v.y});
+                    si = pcal_df::add(si, df{v.z, v.w});
+                }
+                sP[t] = make_float2(sr.hi + sr.lo, si.hi + si.lo);
+            }
         }
-        if (i < N && gs == 0) sT[i] = make_float2(sre, sim);
+    }
+    cluster.sync();  // P is complete in CTA 0; the other CTAs' Pr is no longer read
+    if (!big) {
+        if (r != 0) return false;
+        dft_range(sP, sTw, N, 0, N, sT);
+    } else {
+        // every CTA: its share of the tones from a copy of P, into CTA 0's sT
+        if (r != 0) {
+            const float2* p0 = cluster.map_shared_rank(sP, 0);
+            for (int i = t; i < N; i += blockDim.x) sP[i] = p0[i];
+        }
+        __syncthreads();
+        dft_range(sP, sTw, N, N * r / C, N * (r + 1) / C, cluster.map_shared_rank(sT, 0));
+        cluster.sync();  // CTA 0 holds every tone; its sP is no longer read
+        if (r != 0) return false;
     }
     __syncthreads();
-    if (t < 32) tone_products_warp(a, sT, pm);
+    if (t < 32) tone_products_warp(a, sT, sm.pm);
     __syncthreads();
-    write_results_block(a, sT, pm);
+    write_results_block(a, sT, sm.pm);
     return true;
 }
 
@@ -733,9 +806,10 @@ __global__ void __launch_bounds__(kClusterThreads) fin_cluster_kernel(FinArgs a)
 
 // Batch finalize: cluster c finalizes channel c of the batch from the
 // channel's device state, then starts the channel's next period.
-__global__ void __launch_bounds__(kClusterThreads) batch_fin_kernel(BatchChan* ch) {
+__global__ void __launch_bounds__(kClusterThreads) batch_fin_kernel(BatchChan* ch, const int* list) {
     namespace cg = cooperative_groups;
-    const int c = (int)(blockIdx.x / cg::this_cluster().num_blocks());
+    const int i = (int)(blockIdx.x / cg::this_cluster().num_blocks());
+    const int c = list ? list[i] : i;
     BatchChan& bc = ch[c];
     const int64_t n_tot = bc.n_abs - bc.period_start;
     FinArgs a{};
@@ -915,7 +989,7 @@ cudaError_t launch_cluster_finalize(const FinArgs& a, int C, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C);
     cfg.blockDim = dim3(kClusterThreads);
-    cfg.dynamicSmemBytes = kClusterPadSmem;
+    cfg.dynamicSmemBytes = cluster_smem_bytes(a.N) + kClusterPadSmem;
     cfg.stream = s;
     cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -934,18 +1008,24 @@ cudaError_t launch_cluster_finalize(const FinArgs& a, int C, cudaStream_t s) {
 cudaError_t prepare_batch_finalize() {
     const int C = cluster_size_for_device();
     if (C == 0) return cudaErrorNotSupported;
-    return C > 8 ? cudaFuncSetAttribute(batch_fin_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)
-                 : cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(batch_fin_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)cluster_smem_bytes(kClusterBigN));
+    if (e == cudaSuccess && C > 8)
+        e = cudaFuncSetAttribute(batch_fin_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return e;
 }
 
 // prepare_batch_finalize() must have succeeded on this device (it makes the
-// CUDA calls that a stream capture does not allow).
-cudaError_t launch_batch_finalize(BatchChan* d_ch, int n_ch, cudaStream_t s) {
+// CUDA calls that a stream capture does not allow).  max_n: the largest N of
+// the batch's channels.
+cudaError_t launch_batch_finalize(BatchChan* d_ch, int n_ch, int max_n, const int* d_list, cudaStream_t s) {
     const int C = cluster_size_for_device();
     if (C == 0) return cudaErrorNotSupported;
+    if (max_n > kClusterBigN) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(n_ch * C);
     cfg.blockDim = dim3(kClusterThreads);
+    cfg.dynamicSmemBytes = cluster_smem_bytes(max_n);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -954,7 +1034,7 @@ cudaError_t launch_batch_finalize(BatchChan* d_ch, int n_ch, cudaStream_t s) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, batch_fin_kernel, d_ch);
+    return cudaLaunchKernelEx(&cfg, batch_fin_kernel, d_ch, d_list);
 }
 
 namespace {

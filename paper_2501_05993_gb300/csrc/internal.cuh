@@ -148,14 +148,16 @@ struct BatchChan {
     long long period_start;     // absolute index of the current period's first sample
 };
 
-// One (channel, column group) of one accumulate call's bulk rows.
+// One (region, column group) of one call's bulk rows.
 struct BatchSeg {
     long long box_start;  // first box in the call's box sequence
     int n_boxes;
     int ch;
+    int map;              // tensor map of its region
     int col0;             // first word column of the group
     int tx_bytes;         // bytes one box delivers
-    long long head;       // samples of the call before its first bulk row
+    int pad;
+    long long head;       // samples of the channel in this call before its first bulk row
 };
 
 // A ragged run (head or tail) of one accumulate call.
@@ -168,4 +170,45 @@ struct BatchPiece {
 };
 
 cudaError_t prepare_batch_finalize();
-cudaError_t launch_batch_finalize(BatchChan* d_ch, int n_ch, cudaStream_t s);
+// Finalize channels list[i] (or i when list is null), i < n, with one cluster each.
+cudaError_t launch_batch_finalize(BatchChan* d_ch, int n, int max_n, const int* d_list, cudaStream_t s);
+
+// ---- host side of the batched fold (shared by pcal_batch_* and the server) ----
+
+#include <vector>
+
+// A contiguous run of one channel's samples in device memory.
+struct BatchRegion {
+    int ch;
+    const uint8_t* ptr;
+    int64_t n;    // samples
+    int64_t off;  // samples of this channel earlier in the same call
+};
+
+// Launch shape of the persistent fold for one schedule.
+struct BatchShape {
+    int wpr, replicas, box_rows, stages, merge_stride, threads, grid, run_boxes, static_pct, min_chunk;
+    uint32_t stage_stride;
+    size_t smem;
+};
+
+// Device descriptors of one call: tensor maps, segments, pieces, samples per
+// channel, and the channels to finalize.
+struct BatchCallDesc {
+    std::vector<uint8_t> blob;  // host image of the device buffer
+    size_t off_maps, off_segs, off_pieces, off_n, off_list;
+    int n_segs, n_pieces, n_list;
+    long long total_boxes;
+};
+
+int batch_shape(const pcal_schedule& sc, int cw_max, int num_sms, BatchShape* s);
+int batch_build(const BatchChan* h_ch, int n_ch, const std::vector<BatchRegion>& regions, const BatchShape& sh,
+                const std::vector<int>& fin_list, BatchCallDesc* out);
+cudaError_t batch_launch_fold(const BatchCallDesc& d, void* d_desc, BatchChan* d_ch, int n_ch,
+                              unsigned long long* d_ctr, const BatchShape& sh, unsigned int* d_err, cudaStream_t s,
+                              int* launches);
+cudaError_t batch_prepare_fold();
+cudaError_t batch_launch_tables(BatchChan& C, const pcal_geometry& g, cudaStream_t s);
+void batch_fill_chan(BatchChan& C, const pcal_geometry& g, double f_comb, int col_cap);
+size_t batch_chan_bytes(const pcal_geometry& g);
+void batch_place_chan(BatchChan& C, const pcal_geometry& g, uint8_t* base);

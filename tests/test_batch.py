@@ -26,6 +26,8 @@ CHANNELS = [
     (16, 4, 1, "i8", 40_000, 1),                                 # L 16, N 4
     (64_000_000, 1_000_000, 20_000, "2bit", 4 * 1_000, 2),       # too short for one bulk row
     (128_000_000, 1_000_000, 50_000, "i8", 0, 0),                # empty this period
+    (1_024_000_000, 1_000_000, 10_000, "i8", 1_500_007, 9),      # N 1024, L 102400: DFT over the cluster
+    (512_000_000, 1_000_000, 30_000, "2bit", 4 * 700_001, 4),    # N 512, L 51200
 ]
 
 
