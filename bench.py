@@ -694,6 +694,85 @@ def run_serve(args):
         print(json.dumps(out))
 
 
+# ---- precision workload: one int8 channel, 16 s, every accumulation variant --------------
+
+PREC_SEED = 2501059932 + 2
+PREC_WORKLOAD = ("int8 (sigma 20), fs 1024 MHz, f_comb 1 MHz (N 1024), f_offset 10 kHz (L 102400), 16.384e9 "
+                 "samples (16 s) streamed in 2^30-sample chunks (not L-aligned), tone amplitude 1e-3 sigma")
+
+
+def run_precision(args):
+    import torch
+
+    import oracle
+    import paper_2501_05993_gb300 as pcal
+    import synth
+    from paper_2501_05993_gb300 import build as libbuild
+
+    torch.cuda.set_device(0)
+    libbuild.build()
+    pcal.load()
+    fs, fc, fo, N = 1_024_000_000, 1_000_000, 10_000, 1024
+    total = int(16.384e9 * args.prec_scale) // 4 * 4
+    chunk = 1 << 30
+    stream = synth.Stream(fs=fs, fc=fc, fo=fo, amp=1e-3, td=12.5e-9, seed=PREC_SEED)
+    plan_i8 = pcal.Plan(fs, fc, fo, "i8")
+    plan_f32 = pcal.Plan(fs, fc, fo, "f32")
+    rot = {v: pcal.RotFold(fs, fc, fo, "i8", v, lanes=args.prec_lanes) for v in ("table", "table_kahan", "dfr")}
+    L = plan_i8.L
+    S = np.zeros(L, dtype=np.int64)  # the oracle's exact bins
+    times = {k: 0.0 for k in ("fold-first int64", "fold-first fp32 compensated", "table", "table_kahan", "dfr")}
+    s_ev, e_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cur = torch.cuda.current_stream()
+
+    def timed(name, fn):
+        s_ev.record(cur)
+        fn()
+        e_ev.record(cur)
+        torch.cuda.synchronize()
+        times[name] += s_ev.elapsed_time(e_ev) / 1e3
+
+    n0 = 0
+    while n0 < total:
+        n = min(chunk, total - n0)
+        host = stream.samples("i8", n0, n)
+        d = torch.from_numpy(host).cuda()
+        timed("fold-first int64", lambda: plan_i8.accumulate(d, n))
+        df32 = d.float()
+        timed("fold-first fp32 compensated", lambda: plan_f32.accumulate(df32, n))
+        del df32
+        for v, r in rot.items():
+            timed(v, lambda r=r: r.accumulate(d, n))
+        S += oracle.sums_i8(host, n0, L)
+        n0 += n
+        del d
+    ref = oracle.tones_from_bins(S.astype(np.float64), fs, fc, fo)
+    results = {"fold-first int64": plan_i8.finalize(), "fold-first fp32 compensated": plan_f32.finalize()}
+    for v, r in rot.items():
+        results[v] = r.finalize()
+        r.close()
+    plan_i8.close()
+    plan_f32.close()
+    scale = float(np.max(np.abs(ref)))
+    sig = np.abs(ref) > 1e-3 * scale
+    variants = {}
+    for name, T in results.items():
+        dphi = np.abs(oracle.wrap(np.angle(T[sig]) - np.angle(ref[sig])))
+        variants[name] = {"max_phase_err_rad": float(dphi.max()), "median_phase_err_rad": float(np.median(dphi)),
+                          "max_phasor_err_rel": float(np.max(np.abs(T - ref)) / scale),
+                          "gsamples_per_s": total / times[name] / 1e9}
+    out = {
+        "metric": "PCal precision: max tone phase error vs the FP64 oracle, fold-first integer path (rad)",
+        "value": variants["fold-first int64"]["max_phase_err_rad"], "unit": "rad", "n_gpus": 1, "steps": 1,
+        "warmup": 0, "ms_per_step": times["fold-first int64"] * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "i64", "data": "synthetic",
+        "config": {"workload": PREC_WORKLOAD, "samples": total, "chunk_samples": chunk, "lanes": args.prec_lanes,
+                   "tones_compared": int(sig.sum())},
+        "variants": variants,
+    }
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -711,7 +790,9 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=4.0, help="serve workload: real-time phase, seconds")
     ap.add_argument("--serve-sat-periods", type=int, default=2)
     ap.add_argument("--serve-budget-gb", type=int, default=40)
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve"],
+    ap.add_argument("--prec-scale", type=float, default=1.0, help="precision workload: fraction of the 16 s")
+    ap.add_argument("--prec-lanes", type=int, default=128)
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "precision"],
                     help="single: the 2-bit single-channel headline workload; batch: 64 mixed channels")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -722,6 +803,8 @@ def main():
         run_batch(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "precision":
+        run_precision(args)
     else:
         run_gpu(args)
 

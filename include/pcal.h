@@ -410,6 +410,37 @@ int pcal_server_drain(pcal_server* server, double timeout_s);
 /* Counters and latency percentiles over all published periods. */
 int pcal_server_get_stats(pcal_server* server, pcal_server_stats* out);
 
+/*
+ * ---- Precision study: the paper's per-sample rotation in FP32 ----------------
+ *
+ * pcal_rotfold_* runs the paper's own route for comparison with the fold-first
+ * integer path: every sample rotated by exp(-j w_o n) (Eq. 3) and added into
+ * bin n mod N (Eq. 2) in FP32, with the rotator from an FP32 table of N_rot
+ * entries (Eq. 4) or from the direct-form second-order resonator (Eq. 9), and
+ * the FP32 sums plain or Kahan-compensated; then the bins are DFT'd in FP64.
+ * Thread (lane, b) sums the samples n = b (mod N) with (n div N) = lane
+ * (mod lanes) in sample order, so every FP32 operation has a fixed order; its
+ * accumulator persists across calls until the finalize.  int8 or float32
+ * samples.  The resonator steps over one thread's samples (N*lanes apart) and
+ * is seeded from the exact FP64 phase at each thread's first sample of a call.
+ */
+#define PCAL_ROT_TABLE 0        /* FP32 rotator table, plain FP32 sums        */
+#define PCAL_ROT_TABLE_KAHAN 1  /* FP32 rotator table, Kahan-compensated sums */
+#define PCAL_ROT_DFR 2          /* FP32 resonator (Eq. 9), plain FP32 sums    */
+
+typedef struct pcal_rotfold pcal_rotfold;
+
+int pcal_rotfold_create(double fs, double f_comb, double f_offset, int N, int sample_format, int variant, int lanes,
+                        pcal_rotfold** out);
+int pcal_rotfold_destroy(pcal_rotfold* r);
+/* samples: DEVICE, n samples continuing the absolute index; asynchronous on stream. */
+int pcal_rotfold_accumulate(pcal_rotfold* r, const void* samples, int64_t n, void* stream);
+/* Lanes added in FP64, N-point DFT in FP64; phasors_out: HOST, 2N doubles (re, im).  Synchronises
+ * `stream`, then clears the accumulators (the absolute index keeps counting). */
+int pcal_rotfold_finalize(pcal_rotfold* r, double* phasors_out, void* stream);
+/* The FP32 accumulators, float [lanes][N][4] = (sum re, sum im, compensation re, compensation im). */
+int pcal_rotfold_get_acc(pcal_rotfold* r, float* host_out);
+
 /* Static name of a status code. */
 const char* pcal_strerror(int code);
 

@@ -144,6 +144,11 @@ def load(path: str | None = None):
         "pcal_batch_get_stats": ([vp, P(Stats)], ci),
         "pcal_batch_autotune": ([vp, P(vp), P(i64), vp, P(Schedule)], ci),
         "pcal_server_stream_bytes": ([P(ServerConfig), P(ChannelDesc), P(i64)], ci),
+        "pcal_rotfold_create": ([dbl, dbl, dbl, ci, ci, ci, ci, P(vp)], ci),
+        "pcal_rotfold_destroy": ([vp], ci),
+        "pcal_rotfold_accumulate": ([vp, vp, i64, vp], ci),
+        "pcal_rotfold_finalize": ([vp, vp, vp], ci),
+        "pcal_rotfold_get_acc": ([vp, vp], ci),
         "pcal_server_create": ([P(ServerConfig), P(vp)], ci),
         "pcal_server_destroy": ([vp], ci),
         "pcal_server_open": ([vp, P(ChannelDesc), P(ci)], ci),
@@ -597,3 +602,52 @@ class Server:
         st = ServerStats()
         _check(load().pcal_server_get_stats(self.handle, ctypes.byref(st)), "pcal_server_get_stats")
         return st.as_dict()
+
+
+# ---- precision study: the paper's per-sample rotation in FP32 -------------------------
+
+PCAL_ROT_TABLE, PCAL_ROT_TABLE_KAHAN, PCAL_ROT_DFR = 0, 1, 2
+ROT_VARIANTS = {"table": PCAL_ROT_TABLE, "table_kahan": PCAL_ROT_TABLE_KAHAN, "dfr": PCAL_ROT_DFR}
+
+
+class RotFold:
+    """Rotate-then-fold in FP32 (the paper's route), for the precision study."""
+
+    def __init__(self, fs, f_comb, f_offset, fmt: str, variant: str, lanes: int = 128, N=None):
+        self.N = int(N if N is not None else round(fs / f_comb))
+        self.lanes = int(lanes)
+        h = ctypes.c_void_p()
+        _check(load().pcal_rotfold_create(float(fs), float(f_comb), float(f_offset), self.N, FORMATS[fmt],
+                                          ROT_VARIANTS[variant], self.lanes, ctypes.byref(h)), "pcal_rotfold_create")
+        self.handle = h.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().pcal_rotfold_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def accumulate(self, samples, n: int, stream=None):
+        _check(load().pcal_rotfold_accumulate(self.handle, _ptr(samples), int(n), _stream(stream)),
+               "pcal_rotfold_accumulate")
+
+    def acc(self) -> np.ndarray:
+        out = np.empty((self.lanes, self.N, 4), dtype=np.float32)
+        _check(load().pcal_rotfold_get_acc(self.handle, out.ctypes.data), "pcal_rotfold_get_acc")
+        return out
+
+    def finalize(self, stream=None) -> np.ndarray:
+        out = np.empty(2 * self.N)
+        _check(load().pcal_rotfold_finalize(self.handle, out.ctypes.data, _stream(stream)), "pcal_rotfold_finalize")
+        return out[0::2] + 1j * out[1::2]
