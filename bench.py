@@ -339,9 +339,35 @@ def run_gpu(args):
                        "td_injected_s": TD},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
         }
+        if world == 1 and not args.no_extras:
+            # the other parts of the headline metric: batched vs plain, serving latency
+            del bufs
+            torch.cuda.empty_cache()
+            out["batched"] = summarize_extra(lambda: run_batch(extra_args(args, steps=10, warmup=3), emit=False),
+                                             ("value", "unit", "ms_per_step", "plain", "graph", "roofline", "config"))
+            torch.cuda.empty_cache()
+            out["serving"] = summarize_extra(lambda: run_serve(extra_args(args), emit=False),
+                                             ("p50_ms", "p99_ms", "periods", "realtime", "saturation", "config"))
         print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def extra_args(args, **kw):
+    a = argparse.Namespace(**vars(args))
+    a.no_cpu_baseline, a.no_e2e = True, True
+    for k, v in kw.items():
+        setattr(a, k, v)
+    return a
+
+
+def summarize_extra(fn, keys):
+    """Run a secondary workload; keep the named keys of its line, or the error."""
+    try:
+        out = fn()
+        return {k: out.get(k) for k in keys} if out else None
+    except Exception as e:  # the headline number stands on its own
+        return {"error": f"{type(e).__name__}: {e}"[:300]}
 
 
 # ---- batched workload: 64 channels of mixed format, rate, offset and length ----------
@@ -399,7 +425,7 @@ def batch_inputs(chans, geoms):
     return bufs, blocks
 
 
-def run_batch(args):
+def run_batch(args, emit=True):
     import torch
 
     import paper_2501_05993_gb300 as pcal
@@ -557,9 +583,10 @@ def run_batch(args):
             "graph": {"value": world * total_samples / (graph_ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": graph_ms},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
         }
-        print(json.dumps(out))
-    if dist is not None:
-        dist.destroy_process_group()
+        if emit:
+            print(json.dumps(out))
+        return out
+    return None
 
 
 # ---- serving workload: 256 live streams, 10 ms chunks, Poisson arrivals ------------------
@@ -599,7 +626,7 @@ def serve_chunks(st, k_chunks: int, chunk_s: float):
     return out
 
 
-def run_serve(args):
+def run_serve(args, emit=True):
     import torch
 
     import paper_2501_05993_gb300 as pcal
@@ -691,7 +718,10 @@ def run_serve(args):
                     "d2h_bytes_per_step": sum((5 * int(round(st["fs"] / st["fc"])) + 3) * 8 for st in streams)},
             "clocks": clk,
         }
-        print(json.dumps(out))
+        if emit:
+            print(json.dumps(out))
+        return out
+    return None
 
 
 # ---- precision workload: one int8 channel, 16 s, every accumulation variant --------------
@@ -790,6 +820,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=4.0, help="serve workload: real-time phase, seconds")
     ap.add_argument("--serve-sat-periods", type=int, default=2)
     ap.add_argument("--serve-budget-gb", type=int, default=40)
+    ap.add_argument("--no-extras", action="store_true", help="single workload: skip the batched and serving summaries")
     ap.add_argument("--prec-scale", type=float, default=1.0, help="precision workload: fraction of the 16 s")
     ap.add_argument("--prec-lanes", type=int, default=128)
     ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "precision"],
