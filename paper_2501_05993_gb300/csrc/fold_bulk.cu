@@ -512,11 +512,28 @@ int bulk_tiling(const pcal_plan* p, int64_t n_rows, BulkTiling* t) {
     BulkTiling z{};
     z.cols_total = cols;
     // column groups of at most 256 words (the TMA box limit), 32-byte wide
+    const int sms_fold = p->num_sms >= 64 ? p->num_sms - kFinalizeReserveSms : p->num_sms;
     int gc = (cols + 255) / 256;
     int cw = (cols + gc - 1) / gc;
     cw = (cw + 7) / 8 * 8;
     if (cw > 256) cw = 256;
     gc = (cols + cw - 1) / cw;
+    // Wide rows (long periods): few row groups per column group leave SMs
+    // idle (e.g. 50 groups x 2 rows on 136 SMs); narrow the groups until the
+    // CTAs fill at least 90 % of a whole number of waves.
+    for (int g = gc; cw > 32; ++g) {
+        const int w = ((cols + g - 1) / g + 7) / 8 * 8;
+        const int gg = (cols + w - 1) / w;
+        const int rows_per = sms_fold / gg > 0 ? sms_fold / gg : 1;
+        const int ctas = gg * rows_per;
+        const int waves = (ctas + sms_fold - 1) / sms_fold;
+        if (10 * ctas >= 9 * waves * sms_fold) {
+            cw = w;
+            gc = gg;
+            break;
+        }
+        if (w <= 32) break;
+    }
     z.col_width = cw;
     z.col_groups = gc;
     const int wpr = (cw + 31) / 32;
@@ -563,8 +580,7 @@ int bulk_tiling(const pcal_plan* p, int64_t n_rows, BulkTiling* t) {
     const int64_t total = (n_rows + box - 1) / box;
     if (total > 0x3fffffff) return -1;
     const int64_t cap = 65535 / box;
-    const int sms = p->num_sms >= 64 ? p->num_sms - kFinalizeReserveSms : p->num_sms;
-    int64_t gr = sms / gc;
+    int64_t gr = sms_fold / gc;
     if (gr < 1) gr = 1;
     if (gr > total) gr = total;
     while ((total + gr - 1) / gr * 2 > cap) ++gr;  // very long inputs: more CTAs
