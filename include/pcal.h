@@ -172,6 +172,22 @@ int pcal_read_results(pcal_plan* plan, double* phasors, double* amp, double* pha
 int pcal_get_delay(pcal_plan* plan, double* td_s, double* sigma_td_s);
 
 /*
+ * Post-processing of the last finalize (synchronises the plan's stream):
+ *   td_peak:  the delay from the time-domain pulse P (the folded, rotated
+ *             bins, Eq. 2-3): the largest |P[b]| and the vertex of the parabola
+ *             through it and its neighbours (the three-point estimate of Sec. 2);
+ *             a delay t_d puts the pulse at b = -t_d*fs (mod N), so
+ *             td_peak = -(b + d)/fs wrapped into [-1/(2 f_comb), 1/(2 f_comb)).
+ *   peak_bin: b + d, the interpolated pulse position in bins.
+ *   bandpass_phase: HOST, N doubles: each tone's unwrapped phase minus the
+ *             weighted LS line (the group-delay-corrected bandpass of Sec. 3);
+ *             NaN when no fit exists.
+ * Any pointer may be NULL.  They live on the device right after the 5N+3
+ * doubles of pcal_result_device.
+ */
+int pcal_read_post(pcal_plan* plan, double* td_peak, double* peak_bin, double* bandpass_phase);
+
+/*
  * pcal_result_device -- device address of the plan's result buffer, laid out
  * as doubles: [0,2N) phasors re/im, [2N,3N) amp, [3N,4N) phase, [4N,5N)
  * unwrapped phase, 5N td, 5N+1 sigma_td, 5N+2 samples integrated.  Owned by
@@ -323,6 +339,9 @@ int pcal_batch_step_graph(pcal_batch* batch, const void* const* samples, const i
 int pcal_batch_read_results(pcal_batch* batch, int channel, double* phasors, double* amp, double* phase,
                             double* unwrapped, double* td, double* sigma);
 
+/* Post-processing of one channel (pcal_read_post's definitions; synchronises). */
+int pcal_batch_read_post(pcal_batch* batch, int channel, double* td_peak, double* peak_bin, double* bandpass_phase);
+
 /* Device address of one channel's result vector (layout of pcal_result_device). */
 int pcal_batch_result_device(const pcal_batch* batch, int channel, const double** out);
 
@@ -372,6 +391,7 @@ typedef struct {
     int64_t n_samples;        /* samples in the period                          */
     double td_s, sigma_td_s;  /* delay and its 1-sigma                          */
     double latency_s;         /* last sample submitted -> results on the host  */
+    double td_peak_s;         /* delay from the time-domain pulse (pcal_read_post) */
 } pcal_server_result;
 
 typedef struct {

@@ -222,7 +222,8 @@ def products(T, M: int, fs: int, fc: int, fo: int) -> dict:
         unwrapped[1:] = psi[0] + np.cumsum(wrap(np.diff(psi)))
     f = np.arange(N, dtype=np.float64) * fc + fo
     w = np.abs(T) ** 2
-    out = {"amp": amp, "phase": psi, "unwrapped": unwrapped, "td": float("nan"), "sigma_td": float("nan")}
+    out = {"amp": amp, "phase": psi, "unwrapped": unwrapped, "td": float("nan"), "sigma_td": float("nan"),
+           "bandpass_phase": np.full(N, np.nan), "td_peak": peak_delay(T, fs)}
     W = w.sum()
     if N >= 2 and W > 0:
         fbar = (w * f).sum() / W
@@ -232,11 +233,35 @@ def products(T, M: int, fs: int, fc: int, fo: int) -> dict:
         if sff > 0:
             slope = sfp / sff
             resid = unwrapped - pbar - slope * (f - fbar)
+            out["bandpass_phase"] = resid  # phase after removing the fitted delay (Sec. 3's corrected bandpass)
             out["td"] = slope / (2 * np.pi)
             if N > 2:
                 # weighted LS slope variance; invariant to the scale of w
                 out["sigma_td"] = math.sqrt(((w * resid ** 2).sum() / (N - 2)) / sff) / (2 * np.pi)
     return out
+
+
+def peak_delay(T, fs: int) -> float:
+    """Delay from the time-domain pulse (Sec. 2: the largest bin of P and a
+    three-point interpolation across its neighbours).  P = IDFT(T), the inverse
+    of T_i = sum_b P[b] exp(-2 pi j i b / N); a delay t_d puts the pulse at
+    b = -t_d fs (mod N).  The vertex of the parabola through |P| at the
+    largest bin and its two neighbours refines the position; the result is
+    wrapped into [-N/(2 fs), N/(2 fs))."""
+    T = np.asarray(T, dtype=np.complex128)
+    N = T.size
+    if N == 0 or not np.any(T):
+        return float("nan")
+    b = np.arange(N)
+    P = np.array([np.sum(T * np.exp(2j * np.pi * np.arange(N) * k / N)) for k in b]) / N
+    mag = np.abs(P)
+    k = int(np.argmax(mag))
+    ym, y0, yp = mag[(k - 1) % N], mag[k], mag[(k + 1) % N]
+    den = ym - 2.0 * y0 + yp
+    delta = 0.5 * (ym - yp) / den if den != 0 else 0.0
+    t = -(k + delta) / fs
+    half = N / (2.0 * fs)
+    return float((t + half) % (2.0 * half) - half)
 
 
 def brute_force(x, n0: int, fs: int, fc: int, fo: int, n_tones: int | None = None):

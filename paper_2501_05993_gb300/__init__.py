@@ -78,7 +78,7 @@ class ServerConfig(ctypes.Structure):
 class ServerResult(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_int32), ("n_tones", ctypes.c_int32), ("period", ctypes.c_int64),
                 ("n_samples", ctypes.c_int64), ("td_s", ctypes.c_double), ("sigma_td_s", ctypes.c_double),
-                ("latency_s", ctypes.c_double)]
+                ("latency_s", ctypes.c_double), ("td_peak_s", ctypes.c_double)]
 
 
 class ServerStats(ctypes.Structure):
@@ -124,6 +124,7 @@ def load(path: str | None = None):
         "pcal_finalize": ([vp, vp], ci),
         "pcal_read_results": ([vp, vp, vp, vp, vp, vp, vp], ci),
         "pcal_get_delay": ([vp, P(dbl), P(dbl)], ci),
+        "pcal_read_post": ([vp, vp, vp, vp], ci),
         "pcal_result_device": ([vp], vp),
         "pcal_get_bins": ([vp, vp], ci),
         "pcal_get_stats": ([vp, P(Stats)], ci),
@@ -140,6 +141,7 @@ def load(path: str | None = None):
         "pcal_batch_step_graph": ([vp, P(vp), P(i64), vp], ci),
         "pcal_batch_read_results": ([vp, ci, vp, vp, vp, vp, vp, vp], ci),
         "pcal_batch_result_device": ([vp, ci, P(vp)], ci),
+        "pcal_batch_read_post": ([vp, ci, vp, vp, vp], ci),
         "pcal_batch_get_bins": ([vp, ci, vp], ci),
         "pcal_batch_get_stats": ([vp, P(Stats)], ci),
         "pcal_batch_autotune": ([vp, P(vp), P(i64), vp, P(Schedule)], ci),
@@ -254,6 +256,21 @@ def pcal_get_delay(plan: int) -> tuple[float, float]:
     return td.value, sg.value
 
 
+def pcal_read_post(plan: int, n_tones: int) -> dict:
+    tp, pb = ctypes.c_double(), ctypes.c_double()
+    bp = np.empty(n_tones)
+    _check(load().pcal_read_post(plan, ctypes.addressof(tp), ctypes.addressof(pb), bp.ctypes.data), "pcal_read_post")
+    return {"td_peak": tp.value, "peak_bin": pb.value, "bandpass_phase": bp}
+
+
+def pcal_batch_read_post(batch: int, channel: int, n_tones: int) -> dict:
+    tp, pb = ctypes.c_double(), ctypes.c_double()
+    bp = np.empty(n_tones)
+    _check(load().pcal_batch_read_post(batch, channel, ctypes.addressof(tp), ctypes.addressof(pb), bp.ctypes.data),
+           "pcal_batch_read_post")
+    return {"td_peak": tp.value, "peak_bin": pb.value, "bandpass_phase": bp}
+
+
 def pcal_result_device(plan: int) -> int:
     return int(load().pcal_result_device(plan) or 0)
 
@@ -350,6 +367,10 @@ class Plan:
 
     def bins(self) -> np.ndarray:
         return pcal_get_bins(self.handle, self.geometry)
+
+    def post(self) -> dict:
+        """Peak delay and corrected bandpass of the last finalize."""
+        return pcal_read_post(self.handle, self.N)
 
     def stats(self) -> dict:
         return pcal_get_stats(self.handle).as_dict()
@@ -504,6 +525,9 @@ class Batch:
     def bins(self, channel: int) -> np.ndarray:
         return pcal_batch_get_bins(self.handle, channel, self.geometry[channel])
 
+    def post(self, channel: int) -> dict:
+        return pcal_batch_read_post(self.handle, channel, int(self.geometry[channel].N))
+
     def stats(self) -> dict:
         return pcal_batch_get_stats(self.handle).as_dict()
 
@@ -593,7 +617,8 @@ class Server:
             return None
         n = r.n_tones
         return {"stream": r.stream, "period": r.period, "n_samples": r.n_samples, "td": r.td_s,
-                "sigma_td": r.sigma_td_s, "latency_s": r.latency_s, "phasors": ph[0:2 * n:2] + 1j * ph[1:2 * n:2]}
+                "sigma_td": r.sigma_td_s, "latency_s": r.latency_s, "td_peak": r.td_peak_s,
+                "phasors": ph[0:2 * n:2] + 1j * ph[1:2 * n:2]}
 
     def drain(self, timeout_s: float = 60.0):
         _check(load().pcal_server_drain(self.handle, float(timeout_s)), "pcal_server_drain")

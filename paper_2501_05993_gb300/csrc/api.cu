@@ -132,11 +132,11 @@ extern "C" int pcal_plan_create(double fs, double f_comb, double f_offset, int N
     if (e == cudaSuccess) e = dalloc(&p->d_twN, Nn);
     if (e == cudaSuccess) e = dalloc(&p->d_P, Nn);
     if (e == cudaSuccess) e = dalloc(&p->d_T, Nn);
-    if (e == cudaSuccess) e = dalloc(&p->d_res, 5 * Nn + 3);
+    if (e == cudaSuccess) e = dalloc(&p->d_res, 6 * Nn + 5);
     if (e == cudaSuccess) e = dalloc(&p->d_ticket, 4);
     if (e == cudaSuccess) e = dalloc(&p->d_err, 4);
     if (e == cudaSuccess) e = dalloc(&p->d_sched, kSchedCounters);
-    if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&p->h_res), (5 * Nn + 3) * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&p->h_res), (6 * Nn + 5) * sizeof(double));
     if (e == cudaSuccess) e = launch_init_twiddles(p, 0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(0);
     if (e != cudaSuccess) {
@@ -289,6 +289,21 @@ extern "C" int pcal_finalize(pcal_plan* p, double* phasors_out) {
     int rc = pcal_finalize_device(p, nullptr);
     if (rc != PCAL_OK) return rc;
     return pcal_read_results(p, phasors_out, nullptr, nullptr, nullptr, nullptr, nullptr);
+}
+
+extern "C" int pcal_read_post(pcal_plan* p, double* td_peak, double* peak_bin, double* bandpass_phase) {
+    if (!p) return PCAL_EINVAL;
+    if (!p->results_valid) return PCAL_EBUSY;
+    const int64_t N = p->g.N;
+    double* h = p->h_res + 5 * N + 3;
+    cudaError_t e = cudaMemcpyAsync(h, p->d_res + 5 * N + 3, (N + 2) * sizeof(double), cudaMemcpyDeviceToHost,
+                                    p->last_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->last_stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (td_peak) *td_peak = h[0];
+    if (peak_bin) *peak_bin = h[1];
+    if (bandpass_phase) memcpy(bandpass_phase, h + 2, N * sizeof(double));
+    return PCAL_OK;
 }
 
 extern "C" int pcal_get_delay(pcal_plan* p, double* td, double* sigma) {

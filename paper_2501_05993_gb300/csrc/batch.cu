@@ -695,6 +695,7 @@ void batch_fill_chan(BatchChan& C, const pcal_geometry& g, double f_comb, int co
     C.c_h = g.format == PCAL_2BIT ? lv[2] - lv[0] : 0.0;
     C.c_hl = g.format == PCAL_2BIT ? lv[3] - lv[2] - lv[1] + lv[0] : 0.0;
     C.two_pi_fc = 6.283185307179586476925 * f_comb;
+    C.fs = (double)g.fs;
 }
 
 // Device bytes of one channel's bins, tables and results (each part 256-byte aligned).
@@ -703,7 +704,7 @@ size_t batch_chan_bytes(const pcal_geometry& g) {
     size_t n = 0;
     if (g.format == PCAL_2BIT) n += align_up(8 * L, 256) + align_up(24 * L, 256);
     if (g.format == PCAL_I8) n += align_up(8 * L, 256);
-    n += align_up(16 * L, 256) + align_up(8 * N, 256) + align_up(8 * (5 * N + 3), 256);
+    n += align_up(16 * L, 256) + align_up(8 * N, 256) + align_up(8 * (6 * N + 5), 256);
     return n;
 }
 
@@ -1029,6 +1030,22 @@ extern "C" int pcal_batch_read_results(pcal_batch* b, int channel, double* phaso
     if (unwrapped) memcpy(unwrapped, r.data() + 4 * N, sizeof(double) * N);
     if (td) *td = r[5 * N];
     if (sigma) *sigma = r[5 * N + 1];
+    return PCAL_OK;
+}
+
+extern "C" int pcal_batch_read_post(pcal_batch* b, int channel, double* td_peak, double* peak_bin,
+                                    double* bandpass_phase) {
+    if (!b || channel < 0 || channel >= b->n) return PCAL_EINVAL;
+    int rc = sync_and_check(b);
+    if (rc != PCAL_OK) return rc;
+    const int64_t N = b->g[channel].N;
+    std::vector<double> r(N + 2);
+    if (cudaMemcpy(r.data(), b->h_ch[channel].res + 5 * N + 3, sizeof(double) * r.size(), cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+        return PCAL_ECUDA;
+    if (td_peak) *td_peak = r[0];
+    if (peak_bin) *peak_bin = r[1];
+    if (bandpass_phase) memcpy(bandpass_phase, r.data() + 2, sizeof(double) * N);
     return PCAL_OK;
 }
 

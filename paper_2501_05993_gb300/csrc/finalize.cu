@@ -65,6 +65,8 @@ struct FinArgs {
     float4* P;     // P[b] as df re (x, y), df im (z, w)
     float2* T;     // FP32 tone phasors
     double* res;
+    double* extra;  // post-processing, N+2 doubles (or null): peak delay, peak position, corrected bandpass phase
+    double fs_hz;
     unsigned int* ticket;
 };
 
@@ -270,6 +272,49 @@ __device__ inline ProductsSmem products_layout(uint8_t* base, int64_t N) {
     return m;
 }
 
+// Post-processing (Sec. 2, Sec. 3): the delay from the time-domain pulse --
+// the largest |P[b]| and the vertex of the parabola through it and its two
+// neighbours; a delay t_d puts the pulse at b = -t_d*fs (mod N) -- into
+// extra[0] (seconds, wrapped into one comb period) and extra[1] (the peak
+// position in bins).  One warp; P is read from `P` (float2, re/im).
+__device__ void peak_delay_warp(const FinArgs& a, const float2* P) {
+    const int N = (int)a.N;
+    const int lane = threadIdx.x & 31;
+    float best = -1.f;
+    int bi = 0;
+#pragma unroll 1
+    for (int b = lane; b < N; b += 32) {
+        const float2 z = P[b];
+        const float v = z.x * z.x + z.y * z.y;
+        if (v > best) {
+            best = v;
+            bi = b;
+        }
+    }
+#pragma unroll 1
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) {
+            best = ov;
+            bi = oi;
+        }
+    }
+    if (lane == 0) {
+        const float2 zm = P[(bi + N - 1) % N], zp = P[(bi + 1) % N];
+        const double ym = sqrt((double)zm.x * zm.x + (double)zm.y * zm.y);
+        const double y0 = sqrt((double)best);
+        const double yp = sqrt((double)zp.x * zp.x + (double)zp.y * zp.y);
+        const double den = ym - 2.0 * y0 + yp;
+        const double pos = bi + (den != 0.0 ? 0.5 * (ym - yp) / den : 0.0);
+        const double half = (double)N / (2.0 * a.fs_hz);
+        double t = -pos / a.fs_hz + half;
+        t -= floor(t / (2.0 * half)) * (2.0 * half);
+        a.extra[0] = best > 0.f ? t - half : __longlong_as_double(0x7ff8000000000000ll);
+        a.extra[1] = pos;
+    }
+}
+
 // Amplitude, phase, unwrapped phase and the weighted LS delay fit over all N
 // tones, from T in shared memory; one CTA.  The first nt threads (whole
 // warps, about 8 tones each) do the arithmetic; all threads then write the
@@ -311,8 +356,11 @@ __device__ void tone_products(const FinArgs& a, const ProductsSmem& m) {
     block_sums_df<3>(s3, m.red, nw);
     const df W = s3[0];
     df td{__int_as_float(0x7fc00000), 0.f}, sig{__int_as_float(0x7fc00000), 0.f};  // NaN until fitted
+    df xbar{0.f, 0.f}, ubar{0.f, 0.f}, slope{0.f, 0.f};
+    bool fitted = false;
     if (N >= 2 && W.hi > 0.f) {
-        const df xbar = pcal_df::div(s3[1], W), ubar = pcal_df::div(s3[2], W);
+        xbar = pcal_df::div(s3[1], W);
+        ubar = pcal_df::div(s3[2], W);
         // centred sums; the residual sum follows from Syy - slope*Sxu
         df s2[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         for (int64_t i = c0; i < c1; ++i) {
@@ -327,7 +375,8 @@ __device__ void tone_products(const FinArgs& a, const ProductsSmem& m) {
         }
         block_sums_df<3>(s2, m.red, nw);
         if (s2[0].hi > 0.f) {
-            const df slope = pcal_df::div(s2[1], s2[0]);  // rad per tone index
+            slope = pcal_df::div(s2[1], s2[0]);  // rad per tone index
+            fitted = true;
             td = pcal_df::div(slope, a.two_pi_fc);
             if (N > 2) {
                 df ssr = pcal_df::sub(s2[2], pcal_df::mul(slope, s2[1]));
@@ -341,6 +390,12 @@ __device__ void tone_products(const FinArgs& a, const ProductsSmem& m) {
         m.out[0] = make_float2(td.hi, td.lo);
         m.out[1] = make_float2(sig.hi, sig.lo);
     }
+    if (a.extra)  // bandpass phase with the fitted delay removed
+        for (int64_t i = c0; i < c1; ++i) {
+            const df r = pcal_df::sub(pcal_df::sub(df{m.un[i].x, m.un[i].y}, ubar),
+                                      pcal_df::mul(slope, pcal_df::sub(df{(float)i, 0.f}, xbar)));
+            a.extra[2 + i] = fitted ? (double)r.hi + (double)r.lo : __longlong_as_double(0x7ff8000000000000ll);
+        }
     __syncthreads();
     // 4. FP64 results, written by all threads
     double* amp = a.res + 2 * N;
@@ -426,6 +481,7 @@ __global__ void fin_fold_kernel(FinArgs a) {
         float2* sP = reinterpret_cast<float2*>(smem + products_bytes(a.N));
         dft_tones<NoAlloc>(a, 0, a.N, sP, sP + a.N, m.T);
         tone_products(a, m);
+        if (a.extra && threadIdx.x < 32) peak_delay_warp(a, sP);
     }
 }
 
@@ -535,8 +591,11 @@ __device__ __noinline__ void tone_products_warp(const FinArgs& a, const float2* 
     warp_sums_df<3>(s3);
     const df W = s3[0];
     df td{__int_as_float(0x7fc00000), 0.f}, sig{__int_as_float(0x7fc00000), 0.f};  // NaN until fitted
+    df xbar{0.f, 0.f}, ubar{0.f, 0.f}, slope{0.f, 0.f};
+    bool fitted = false;
     if (N >= 2 && W.hi > 0.f) {
-        const df xbar = pcal_df::div(s3[1], W), ubar = pcal_df::div(s3[2], W);
+        xbar = pcal_df::div(s3[1], W);
+        ubar = pcal_df::div(s3[2], W);
         // centred sums; the residual sum follows from Syy - slope*Sxu
         df s2[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
 #pragma unroll 1
@@ -551,7 +610,8 @@ __device__ __noinline__ void tone_products_warp(const FinArgs& a, const float2* 
         }
         warp_sums_df<3>(s2);
         if (s2[0].hi > 0.f) {
-            const df slope = pcal_df::div(s2[1], s2[0]);  // rad per tone index
+            slope = pcal_df::div(s2[1], s2[0]);  // rad per tone index
+            fitted = true;
             td = pcal_df::div(slope, a.two_pi_fc);
             if (N > 2) {
                 df ssr = pcal_df::sub(s2[2], pcal_df::mul(slope, s2[1]));
@@ -564,6 +624,15 @@ __device__ __noinline__ void tone_products_warp(const FinArgs& a, const float2* 
     if (lane == 0) {
         m.out[0] = make_float2(td.hi, td.lo);
         m.out[1] = make_float2(sig.hi, sig.lo);
+    }
+    if (a.extra) {
+        // bandpass phase with the fitted delay removed: u_i - ubar - slope*(i - xbar)
+#pragma unroll 1
+        for (int i = i0; i < i1; ++i) {
+            const df r = pcal_df::sub(pcal_df::sub(df{m.un[i].x, m.un[i].y}, ubar),
+                                      pcal_df::mul(slope, pcal_df::sub(df{(float)i, 0.f}, xbar)));
+            a.extra[2 + i] = fitted ? (double)r.hi + (double)r.lo : __longlong_as_double(0x7ff8000000000000ll);
+        }
     }
 }
 
@@ -791,6 +860,7 @@ __device__ __forceinline__ bool cluster_finalize(const FinArgs& a) {
     }
     __syncthreads();
     if (t < 32) tone_products_warp(a, sT, sm.pm);
+    else if (t < 64 && a.extra) peak_delay_warp(a, sP);
     __syncthreads();
     write_results_block(a, sT, sm.pm);
     return true;
@@ -835,6 +905,8 @@ __global__ void __launch_bounds__(kClusterThreads) batch_fin_kernel(BatchChan* c
     a.tw = bc.tw;
     a.twN = bc.twN;
     a.res = bc.res;
+    a.extra = bc.res + 5 * bc.N + 3;
+    a.fs_hz = bc.fs;
     // every CTA has read the state above before the first cluster barrier
     // inside, and rank 0 returns after the last one
     if (cluster_finalize(a) && threadIdx.x == 0) bc.period_start = bc.n_abs;
@@ -862,6 +934,17 @@ __global__ void fin_dft_kernel(FinArgs a) {
     for (int64_t i = threadIdx.x; i < a.N; i += blockDim.x) m.T[i] = __ldcg(&a.T[i]);
     __syncthreads();
     tone_products(a, m);
+    if (a.extra) {
+        // P again, into the shared memory the products no longer need
+        __syncthreads();
+        float2* sP = reinterpret_cast<float2*>(smem);
+        for (int64_t b = threadIdx.x; b < a.N; b += blockDim.x) {
+            const float4 v = __ldcg(&a.P[b]);
+            sP[b] = make_float2(v.x + v.y, v.z + v.w);
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) peak_delay_warp(a, sP);
+    }
 }
 
 __global__ void init_twiddles_kernel(double2* tw, int64_t L, float2* twN, int64_t N, int64_t sc) {
@@ -1040,6 +1123,7 @@ cudaError_t launch_batch_finalize(BatchChan* d_ch, int n_ch, int max_n, const in
 namespace {
 
 void set_common(FinArgs& a, const pcal_geometry& g, int64_t n_tot) {
+    a.fs_hz = (double)g.fs;
     a.L = g.L;
     a.N = g.N;
     a.so = g.step_offset;
@@ -1076,6 +1160,7 @@ cudaError_t launch_finalize(pcal_plan* p, cudaStream_t s) {
     a.P = reinterpret_cast<float4*>(p->d_P);
     a.T = reinterpret_cast<float2*>(p->d_T);
     a.res = p->d_res;
+    a.extra = p->d_res + 5 * g.N + 3;
     a.ticket = p->d_ticket;
     if (g.N <= kClusterMaxN && g.L <= kClusterMaxL) {
         const int C = cluster_size_for_device();

@@ -80,7 +80,7 @@ struct pcal_plan {
     float2* d_twN;                // exp(-j 2 pi m / N), m < N (FP32)
     double2* d_P;                 // folded rotated bins P[b], b < N (scratch)
     double2* d_T;                 // tone phasors (scratch before products)
-    double* d_res;                // results, 5N+3 doubles
+    double* d_res;                // results, 5N+3 doubles, then the post-processing, N+2 doubles
     unsigned int* d_ticket;       // [0] fold ticket, [1] dft ticket
     unsigned int* d_err;          // device error flags
     unsigned long long* d_sched;  // bulk kernel box counters [kSchedCounters]: (epoch << 32) | boxes
@@ -141,9 +141,10 @@ struct BatchChan {
     long long* acc8;            // int8: [L] sums
     const double2* tw;          // exp(-j 2 pi m / L), m < L
     const float2* twN;          // exp(-j 2 pi m / N), m < N
-    double* res;                // 5N+3 results
+    double* res;                // 5N+3 results, then N+2 post-processing values
     double lev0, c_l, c_h, c_hl;
     double two_pi_fc;
+    double fs;
     long long n_abs;            // samples accumulated since creation
     long long period_start;     // absolute index of the current period's first sample
 };

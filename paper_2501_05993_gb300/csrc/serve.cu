@@ -195,6 +195,7 @@ void CUDART_CB iteration_done(void* p) {
             pub.r.td_s = st.h_res[5 * N];
             pub.r.sigma_td_s = st.h_res[5 * N + 1];
             pub.r.latency_s = t - t_arr;
+            pub.r.td_peak_s = st.h_res[5 * N + 3];
             pub.phasors.assign(st.h_res, st.h_res + 2 * N);
             s->latencies.push_back(pub.r.latency_s);
             s->results.push_back(std::move(pub));
@@ -354,7 +355,7 @@ void worker_loop(pcal_server* s) {
             for (const IterInfo::Fin& f : info->fins) {
                 if (e != cudaSuccess) break;
                 const SrvStream& st = s->streams[f.id];
-                e = cudaMemcpyAsync(st.h_res, s->h_ch[st.slot].res, sizeof(double) * (5 * st.g.N + 3),
+                e = cudaMemcpyAsync(st.h_res, s->h_ch[st.slot].res, sizeof(double) * (6 * st.g.N + 5),
                                     cudaMemcpyDeviceToHost, s->compute);
             }
         }
@@ -479,7 +480,7 @@ extern "C" int pcal_server_open(pcal_server* s, const pcal_channel_desc* desc, i
     const int rc = stream_layout(s->cfg, *desc, &st);
     if (rc != PCAL_OK) return rc;
     if (align_up(st.bytes, 256) > (size_t)s->cfg.hbm_budget_bytes) return PCAL_ENOMEM;
-    if (cudaMallocHost(&st.h_res, sizeof(double) * (5 * st.g.N + 3)) != cudaSuccess) return PCAL_ENOMEM;
+    if (cudaMallocHost(&st.h_res, sizeof(double) * (6 * st.g.N + 5)) != cudaSuccess) return PCAL_ENOMEM;
     std::lock_guard<std::mutex> lk(s->mu);
     st.id = (int)s->streams.size();
     s->streams.push_back(st);

@@ -99,6 +99,12 @@ def check_results(batch, c, ch, host, n0=0):
     scale = np.max(np.abs(ref))
     assert np.max(np.abs(T - ref)) <= PHASOR_RTOL * scale, (c, np.max(np.abs(T - ref)) / scale)
     assert np.allclose(res["amp"], 2 * np.abs(T) / n, rtol=1e-6)
+    post = batch.post(c)
+    pref = oracle.products(ref, n, fs, fc, fo)
+    assert abs(post["td_peak"] - pref["td_peak"]) <= 1e-3 / fs
+    mag = np.abs(ref)
+    if np.all(np.isfinite(pref["bandpass_phase"])) and mag.min() > 0.05 * mag.max():  # unwrapping well defined
+        assert np.max(np.abs(post["bandpass_phase"] - pref["bandpass_phase"])) < 1e-3
     return res
 
 

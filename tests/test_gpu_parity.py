@@ -189,6 +189,32 @@ def test_products_and_delay(pcal):
     assert abs(r["td"] - td) < 5 * ref["sigma_td"]  # physics: delay recovered
 
 
+@pytest.mark.parametrize("plan_name", ["c2", "c1", "odd", "long", "wide"])
+def test_peak_delay_and_bandpass(pcal, plan_name):
+    """Post-processing (cluster and completion-ticket finalizes): the delay
+    from the time-domain pulse and the delay-corrected bandpass phase against
+    the oracle's, on a strong comb (float32, so no 2-bit intermodulation)."""
+    fs, fc, fo = PLANS[plan_name]
+    L = oracle.plan(fs, fc, fo)["L"]
+    n = max(2 * L, 2_000_000) // L * L
+    td = 17.3 / fs
+    host = synth.Stream(fs=fs, fc=fc, fo=fo, amp=0.2, td=td, seed=5).f32(0, n)
+    with pcal.Plan(fs, fc, fo, "f32") as p:
+        keep, addr = to_dev(host, 4)
+        p.accumulate(addr, n)
+        T = p.finalize()
+        post = p.post()
+    ref = oracle.products(oracle.tones_from_bins(oracle.bins(host, "f32", 0, L), fs, fc, fo), n, fs, fc, fo)
+    N = fs // fc
+    assert abs(post["td_peak"] - ref["td_peak"]) <= 1e-3 / fs
+    half = N / (2 * fs)
+    assert abs(post["td_peak"] - ((td + half) % (2 * half) - half)) < 0.25 / fs  # the pulse is where td puts it
+    ok = np.isfinite(ref["bandpass_phase"])
+    assert ok.all()
+    assert np.max(np.abs(post["bandpass_phase"] - ref["bandpass_phase"])) < PHASE_ATOL
+    assert np.max(np.abs(post["bandpass_phase"])) < 0.05  # a flat band once the delay is removed
+
+
 def test_empty_and_invalid(pcal):
     with pcal.Plan(64_000_000, 1_000_000, 10_000, "2bit") as p:
         p.accumulate(0, 0)  # no-op

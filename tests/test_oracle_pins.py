@@ -122,6 +122,34 @@ def test_products_closed_form():
     assert abs(pr["td"] - td) < 1e-12 * td + 1e-18
 
 
+@pytest.mark.parametrize("shift", [3, 11, 62])
+def test_peak_delay_integer_shift(shift):
+    """A noise-free comb whose delay is a whole number of samples puts the
+    whole pulse in one bin of P: the peak estimate is the delay exactly
+    (wrapped into one comb period), and the corrected bandpass is flat."""
+    fs, fc, fo, amp = 64000, 1000, 10, 0.01
+    td = shift / fs
+    L = oracle.plan(fs, fc, fo)["L"]
+    M = 2 * L
+    x = synth.Stream(fs=fs, fc=fc, fo=fo, amp=amp, td=td, sigma=0.0).real(0, M)
+    pr = oracle.products(oracle.direct(x, "f64", 0, fs, fc, fo), M, fs, fc, fo)
+    N = fs // fc
+    want = ((td + N / (2 * fs)) % (N / fs)) - N / (2 * fs)
+    assert abs(pr["td_peak"] - want) < 1e-12
+    assert np.max(np.abs(pr["bandpass_phase"])) < 1e-9
+
+
+def test_peak_delay_fractional_shift():
+    """Between samples the three-point estimate lands within a quarter sample."""
+    fs, fc, fo, amp = 64000, 1000, 10, 0.01
+    L = oracle.plan(fs, fc, fo)["L"]
+    for frac in (0.2, 0.5, 0.8):
+        td = (5 + frac) / fs
+        x = synth.Stream(fs=fs, fc=fc, fo=fo, amp=amp, td=td, sigma=0.0).real(0, L)
+        pr = oracle.products(oracle.direct(x, "f64", 0, fs, fc, fo), L, fs, fc, fo)
+        assert abs(pr["td_peak"] - td) < 0.25 / fs, (frac, pr["td_peak"] * fs)
+
+
 # ---------------------------------------------------------- library routine
 
 @pytest.mark.parametrize("fmt", ["f32", "i8", "2bit", "f64"])
