@@ -67,6 +67,7 @@ def _load():
         lib.orc_get_mutation.restype = ci
         lib.orc_plan.argtypes = [i64, i64, i64, vp, vp, vp, vp]
         lib.orc_direct.argtypes = [vp, ci, vp, i64, i64, i64, i64, i64, i64, vp]
+        lib.orc_direct_dy.argtypes = [vp, ci, vp, i64, i64, i64, i64, i64, ci, i64, vp]
         lib.orc_fold_real.argtypes = [vp, ci, vp, i64, i64, i64, vp]
         lib.orc_tones_from_bins.argtypes = [vp, i64, i64, i64, i64, vp]
         lib.orc_rotate_fold_dft.argtypes = [vp, i64, i64, i64, vp]
@@ -130,6 +131,26 @@ def direct(samples, fmt: str, n0: int, fs: int, fc: int, fo: int, n_tones: int |
                             out.ctypes.data)
     if rc:
         raise ValueError(f"orc_direct failed ({rc})")
+    return out[0::2] + 1j * out[1::2]
+
+
+def direct_any(samples, fmt: str, n0: int, fs: int, fc: int, fo: float, n_tones: int | None = None,
+               levels=DEFAULT_LEVELS, M: int | None = None) -> np.ndarray:
+    """The direct definition for an offset that is any binary fraction of a
+    hertz (fo = num / 2**shift exactly): prime or non-integral offsets."""
+    num, den = float(fo).as_integer_ratio()
+    shift = den.bit_length() - 1
+    if den != 1 << shift or num < 0:
+        raise ValueError("offset must be a non-negative binary fraction")
+    a = _samples(samples, fmt)
+    M = _count(a, fmt, M)
+    n_tones = fs // fc if n_tones is None else int(n_tones)
+    out = np.zeros(2 * n_tones, dtype=np.float64)
+    lev = _levels(levels)
+    rc = _load().orc_direct_dy(a.ctypes.data, FORMATS[fmt], lev.ctypes.data, M, int(n0), fs, fc, num, shift,
+                               n_tones, out.ctypes.data)
+    if rc:
+        raise ValueError(f"orc_direct_dy failed ({rc})")
     return out[0::2] + 1j * out[1::2]
 
 

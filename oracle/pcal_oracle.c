@@ -142,6 +142,39 @@ int orc_direct(const void* buf, int fmt, const double* levels, int64_t M, int64_
 }
 
 /*
+ * Direct definition for any offset that is a binary fraction of a hertz,
+ * f_offset = fo_num / 2^fo_shift (prime offsets whose period L is too long to
+ * fold, and non-integral offsets):
+ *   T_i = sum_t x[t] exp(-j*2*pi*((i*fc*2^s + fo_num)*(n0+t) mod (fs*2^s)) / (fs*2^s)),
+ * the phase reduced exactly in 128-bit integers, cos/sin per term, Neumaier sums.
+ */
+int orc_direct_dy(const void* buf, int fmt, const double* levels, int64_t M, int64_t n0, int64_t fs, int64_t fc,
+                  int64_t fo_num, int fo_shift, int64_t n_tones, double* out) {
+    typedef __int128 i128;
+    if (M < 0 || n0 < 0 || fs <= 0 || fc <= 0 || fo_num < 0 || fo_shift < 0 || fo_shift > 60) return -1;
+    if (g_mutation == MUT_DROP_N0) n0 = 0;
+    const i128 mod = (i128)fs << fo_shift;
+    const double sgn = (g_mutation == MUT_ROT_SIGN) ? 1.0 : -1.0;
+    for (int64_t i = 0; i < n_tones; ++i) {
+        int64_t ii = (g_mutation == MUT_TONE_INDEX) ? i + 1 : i;
+        const i128 a = ((((i128)ii * fc) << fo_shift) + fo_num) % mod;
+        i128 r = (a * (i128)n0) % mod;
+        nsum re = {0, 0}, im = {0, 0};
+        for (int64_t t = 0; t < M; ++t) {
+            const double x = sample_at(buf, fmt, t, levels);
+            const double ang = 6.283185307179586476925 * ((double)r / (double)mod);
+            nadd(&re, x * cos(ang));
+            nadd(&im, x * sgn * sin(ang));
+            r += a;
+            if (r >= mod) r -= mod;
+        }
+        out[2 * i] = nval(&re);
+        out[2 * i + 1] = nval(&im);
+    }
+    return 0;
+}
+
+/*
  * Fold of the raw stream modulo L (Eq. 2 with the combined period):
  * S[k] = sum_{t : (n0+t) mod L == k} x[t], FP64 with compensation.
  */

@@ -50,6 +50,11 @@ def _load():
         lib.synth_real.restype = ctypes.c_int
         lib.synth_quantized.argtypes = [u64, u32, i64, i64, dbl, i64, i64, i64, i64, dbl, dbl, ctypes.c_int, dbl, vp]
         lib.synth_quantized.restype = ctypes.c_int
+        ci = ctypes.c_int
+        lib.synth_real_dy.argtypes = [u64, u32, i64, i64, dbl, i64, i64, i64, ci, i64, dbl, dbl, vp]
+        lib.synth_real_dy.restype = ci
+        lib.synth_quantized_dy.argtypes = [u64, u32, i64, i64, dbl, i64, i64, i64, ci, i64, dbl, dbl, ci, dbl, vp]
+        lib.synth_quantized_dy.restype = ci
         _lib = lib
     return _lib
 
@@ -64,13 +69,27 @@ def philox4x32(ctr, key, rounds: int = 10):
     return [int(v) for v in o]
 
 
+TABLE_MAX_L = 1 << 22  # longer comb periods are evaluated sample by sample
+
+
+def dyadic(f) -> tuple[int, int]:
+    """(num, shift) with f = num / 2**shift exactly (any finite binary float >= 0)."""
+    num, den = float(f).as_integer_ratio()
+    shift = den.bit_length() - 1
+    if den != 1 << shift or num < 0:
+        raise ValueError(f"offset {f!r} is not a non-negative binary fraction")
+    return num, shift
+
+
 @dataclass(frozen=True)
 class Stream:
-    """One synthetic baseband channel (all frequencies in integral Hz)."""
+    """One synthetic baseband channel: integral fs and fc; fo integral, or any
+    binary fraction of a hertz (then, or when the comb period is longer than
+    TABLE_MAX_L, the comb is evaluated sample by sample)."""
 
     fs: int
     fc: int
-    fo: int
+    fo: float
     amp: float          # tone amplitude A in units of the noise sigma
     td: float           # injected instrumental delay in seconds
     sigma: float = 1.0  # noise standard deviation (0 gives the noise-free comb)
@@ -86,33 +105,49 @@ class Stream:
         return (self.seed, self.stream, int(n0), int(count), float(self.sigma), int(self.fs), int(self.fc),
                 int(self.fo), int(self.N), float(self.amp), float(self.td))
 
+    def _direct(self) -> bool:
+        if float(self.fo) != int(self.fo):
+            return True
+        import math
+
+        return self.fs // math.gcd(math.gcd(int(self.fs), int(self.fc)), int(self.fo)) > TABLE_MAX_L
+
+    def _args_dy(self, n0: int, count: int):
+        num, shift = dyadic(self.fo)
+        return (self.seed, self.stream, int(n0), int(count), float(self.sigma), int(self.fs), int(self.fc), num,
+                shift, int(self.N), float(self.amp), float(self.td))
+
+    def _quantized(self, n0, count, fmt, param, out):
+        lib = _load()
+        if self._direct():
+            rc = lib.synth_quantized_dy(*self._args_dy(n0, count), fmt, float(param), out.ctypes.data)
+        else:
+            rc = lib.synth_quantized(*self._args(n0, count), fmt, float(param), out.ctypes.data)
+        if rc != 0:
+            raise ValueError("synth_quantized: bad arguments")
+        return out
+
     def real(self, n0: int, count: int) -> np.ndarray:
         """Unquantised FP64 samples for absolute indices n0 .. n0+count-1."""
         out = np.empty(int(count), dtype=np.float64)
-        if _load().synth_real(*self._args(n0, count), out.ctypes.data) != 0:
+        lib = _load()
+        rc = (lib.synth_real_dy(*self._args_dy(n0, count), out.ctypes.data) if self._direct()
+              else lib.synth_real(*self._args(n0, count), out.ctypes.data))
+        if rc != 0:
             raise ValueError("synth_real: bad arguments")
         return out
 
     def f32(self, n0: int, count: int) -> np.ndarray:
-        out = np.empty(int(count), dtype=np.float32)
-        if _load().synth_quantized(*self._args(n0, count), FMT_F32, 0.0, out.ctypes.data) != 0:
-            raise ValueError("synth_quantized: bad arguments")
-        return out
+        return self._quantized(n0, count, FMT_F32, 0.0, np.empty(int(count), dtype=np.float32))
 
     def i8(self, n0: int, count: int, scale: float = 20.0) -> np.ndarray:
-        out = np.empty(int(count), dtype=np.int8)
-        if _load().synth_quantized(*self._args(n0, count), FMT_I8, float(scale), out.ctypes.data) != 0:
-            raise ValueError("synth_quantized: bad arguments")
-        return out
+        return self._quantized(n0, count, FMT_I8, scale, np.empty(int(count), dtype=np.int8))
 
     def bits2(self, n0: int, count: int, threshold: float = 0.98) -> np.ndarray:
         """2-bit packed bytes; count must be a multiple of 4."""
         if count % 4:
             raise ValueError("2-bit streams hold whole bytes: count must be a multiple of 4")
-        out = np.empty(int(count) // 4, dtype=np.uint8)
-        if _load().synth_quantized(*self._args(n0, count), FMT_2BIT, float(threshold), out.ctypes.data) != 0:
-            raise ValueError("synth_quantized: bad arguments")
-        return out
+        return self._quantized(n0, count, FMT_2BIT, threshold, np.empty(int(count) // 4, dtype=np.uint8))
 
     def samples(self, fmt: str, n0: int, count: int) -> np.ndarray:
         if fmt == "f32":

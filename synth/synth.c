@@ -116,6 +116,36 @@ static int64_t comb_table(int64_t fs, int64_t fc, int64_t fo, int64_t N, double 
 }
 
 /*
+ * Offsets that are not whole hertz, or whose period L is too long to tabulate:
+ * f_offset = fo_num / 2^fo_shift exactly (every binary fraction is such a
+ * ratio), tone i at f_i = (i*fc*2^s + fo_num) / 2^s.  Its phase at sample n
+ * is 2*pi*((i*fc*2^s + fo_num)*n mod (fs*2^s)) / (fs*2^s) + 2*pi*f_i*td,
+ * reduced exactly in 128-bit integers; the comb is summed tone by tone.
+ * Returns the comb values for n0 .. n0+count-1 into p (count doubles).
+ */
+typedef __int128 i128;
+static int comb_direct(int64_t fs, int64_t fc, int64_t fo_num, int fo_shift, int64_t N, double A, double td,
+                       int64_t n0, int64_t count, double* p) {
+    if (fs <= 0 || fc <= 0 || fo_num < 0 || fo_shift < 0 || fo_shift > 60 || N < 0) return -1;
+    for (int64_t t = 0; t < count; ++t) p[t] = 0.0;
+    if (A == 0.0) return 0;
+    const i128 mod = (i128)fs << fo_shift;
+    for (int64_t i = 0; i < N; ++i) {
+        const i128 a = (((i128)i * fc) << fo_shift) + fo_num; /* f_i * 2^s                 */
+        const double fi = (double)a / ldexp(1.0, fo_shift);
+        const double phi = 6.283185307179586476925 * fmod(fi * td, 1.0);
+        const i128 step = a % mod;
+        i128 r = (step * (i128)n0) % mod;                     /* (a*n) mod (fs*2^s), exact */
+        for (int64_t t = 0; t < count; ++t) {
+            p[t] += A * sin(6.283185307179586476925 * ((double)r / (double)mod) + phi);
+            r += step;
+            if (r >= mod) r -= mod;
+        }
+    }
+    return 0;
+}
+
+/*
  * Real samples x[n] for absolute indices n0 .. n0+count-1, written as FP64.
  * The noise of absolute index n comes from pair m = n/2 (even n: first normal).
  */
@@ -203,4 +233,70 @@ int synth_quantized(uint64_t seed, uint32_t stream, int64_t n0, int64_t count, d
     (void)err;
     free(p);
     return 0;
+}
+
+/*
+ * As synth_real / synth_quantized for an offset fo_num / 2^fo_shift Hz (see
+ * comb_direct): the comb is evaluated sample by sample, in blocks.
+ */
+int synth_real_dy(uint64_t seed, uint32_t stream, int64_t n0, int64_t count, double sigma, int64_t fs, int64_t fc,
+                  int64_t fo_num, int fo_shift, int64_t N, double A, double td, double* out) {
+    if (n0 < 0 || count < 0) return -1;
+    int err = 0;
+#pragma omp parallel for schedule(static)
+    for (int64_t blk = 0; blk < (count + 4095) / 4096; ++blk) {
+        int64_t s = blk * 4096, e = s + 4096 < count ? s + 4096 : count;
+        if (comb_direct(fs, fc, fo_num, fo_shift, N, A, td, n0 + s, e - s, out + s) != 0) {
+            err = 1;
+            continue;
+        }
+        for (int64_t t = s; t < e; ++t) {
+            int64_t n = n0 + t;
+            if (sigma != 0.0) {
+                double z0, z1;
+                normal_pair(seed, stream, (uint64_t)n >> 1, &z0, &z1);
+                out[t] += sigma * ((n & 1) ? z1 : z0);
+            }
+        }
+    }
+    return err ? -1 : 0;
+}
+
+int synth_quantized_dy(uint64_t seed, uint32_t stream, int64_t n0, int64_t count, double sigma, int64_t fs,
+                       int64_t fc, int64_t fo_num, int fo_shift, int64_t N, double A, double td, int fmt, double param,
+                       void* out) {
+    if (n0 < 0 || count < 0) return -1;
+    if (fmt == 2 && (count % 4) != 0) return -1;
+    int err = 0;
+#pragma omp parallel for schedule(static)
+    for (int64_t blk = 0; blk < (count + 4095) / 4096; ++blk) {
+        int64_t s = blk * 4096, e = s + 4096 < count ? s + 4096 : count;
+        double x[4096];
+        if (comb_direct(fs, fc, fo_num, fo_shift, N, A, td, n0 + s, e - s, x) != 0) {
+            err = 1;
+            continue;
+        }
+        uint8_t acc = 0;
+        for (int64_t t = s; t < e; ++t) {
+            int64_t n = n0 + t;
+            double v = x[t - s];
+            if (sigma != 0.0) {
+                double z0, z1;
+                normal_pair(seed, stream, (uint64_t)n >> 1, &z0, &z1);
+                v += sigma * ((n & 1) ? z1 : z0);
+            }
+            if (fmt == 0) {
+                ((float*)out)[t] = (float)v;
+            } else if (fmt == 1) {
+                ((int8_t*)out)[t] = quant8(v, param);
+            } else {
+                acc |= (uint8_t)(code2(v, param) << (2 * (t & 3)));
+                if ((t & 3) == 3) {
+                    ((uint8_t*)out)[t >> 2] = acc;
+                    acc = 0;
+                }
+            }
+        }
+    }
+    return err ? -1 : 0;
 }

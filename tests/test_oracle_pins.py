@@ -8,6 +8,7 @@ mod L), values the paper prints (tests/golden/paper_constants.json), or
 invariants.  test_planted_mistakes shows that each plausible mistake planted
 in the oracle breaks at least one pin.
 """
+import cmath
 import json
 import math
 import os
@@ -340,3 +341,84 @@ def test_planted_mistakes(code):
     with oracle.mutation(code):
         failed = _pin_battery()
     assert failed, f"mutation {code} went unnoticed"
+
+
+# ---------------------------------------------------------- offsets beyond the fold
+
+def comb_closed_form_dyadic(fs, fc, num, shift, amp, td, n0, M):
+    """Exact T_i of the noise-free comb for f_offset = num / 2**shift, by the
+    geometric series of each exponential with its phase reduced in integers
+    modulo fs * 2**shift."""
+    N = fs // fc
+    mod = fs << shift
+    out = np.zeros(N, dtype=np.complex128)
+
+    def geo(a):
+        a %= mod
+        start = np.exp(2j * np.pi * ((a * n0) % mod) / mod)
+        if a == 0:
+            return start * M
+        z = np.exp(2j * np.pi * a / mod)
+        zM = np.exp(2j * np.pi * ((a * M) % mod) / mod)
+        return start * (1 - zM) / (1 - z)
+
+    for i in range(N):
+        ai = (i * fc << shift) + num                 # f_i * 2**shift
+        phi = 2 * np.pi * math.fmod(ai / (1 << shift) * td, 1.0)
+        acc = 0j
+        for k in range(N):
+            ak = (k * fc << shift) + num
+            phik = 2 * np.pi * math.fmod(ak / (1 << shift) * td, 1.0)
+            # sin(u) = (e^{ju} - e^{-ju}) / 2j, summed against e^{-j theta_i n}
+            acc += amp / 2j * (np.exp(1j * phik) * geo(ak - ai) - np.exp(-1j * phik) * geo(-ak - ai))
+        out[i] = acc
+    return out
+
+
+@pytest.mark.parametrize("fo", [10007.0, 10007.25, 333.125])
+def test_direct_any_closed_form(fo):
+    """A prime and two fractional offsets: the oracle's direct definition equals
+    the exact geometric-series sum of the noise-free comb."""
+    fs, fc, amp, td, n0, M = 64000, 8000, 0.3, 2.5e-6, 777, 20011
+    num, den = float(fo).as_integer_ratio()
+    shift = den.bit_length() - 1
+    x = synth.Stream(fs=fs, fc=fc, fo=fo, amp=amp, td=td, sigma=0.0).real(n0, M)
+    T = oracle.direct_any(x, "f64", n0, fs, fc, fo)
+    assert rel(T, comb_closed_form_dyadic(fs, fc, num, shift, amp, td, n0, M)) < 1e-9
+
+
+def test_direct_any_brute_force_exact_rationals():
+    """Tiny input: pure Python with exact rational phases."""
+    from fractions import Fraction
+
+    fs, fc, fo = 32, 8, 3.375
+    x = synth.Stream(fs=fs, fc=fc, fo=fo, amp=0.5, td=0.01, seed=4).real(5, 300)
+    N = fs // fc
+    ref = []
+    for i in range(N):
+        f = Fraction(i * fc) + Fraction(fo)
+        acc = 0j
+        for t, v in enumerate(x):
+            cyc = (f * (5 + t) / fs) % 1
+            acc += v * cmath.exp(-2j * math.pi * float(cyc))
+        ref.append(acc)
+    assert rel(oracle.direct_any(x, "f64", 5, fs, fc, fo), np.array(ref)) < 1e-12
+
+
+def test_direct_any_integral_offset_is_the_definition():
+    """For an integral offset with a short period both routes of the oracle
+    evaluate the same sum."""
+    fs, fc, fo = 16000, 1000, 10
+    x = synth.Stream(fs=fs, fc=fc, fo=fo, amp=0.2, td=1e-5, seed=6).i8(3, 40000)
+    assert rel(oracle.direct_any(x, "i8", 3, fs, fc, fo), oracle.direct(x, "i8", 3, fs, fc, fo)) < 1e-11
+
+
+@pytest.mark.parametrize("code", [1, 2, 3])
+def test_direct_any_planted_mistakes(code):
+    fs, fc, amp, td, n0, M, fo = 64000, 8000, 0.3, 2.5e-6, 777, 20011, 10007.25
+    num, den = float(fo).as_integer_ratio()
+    x = synth.Stream(fs=fs, fc=fc, fo=fo, amp=amp, td=td, sigma=0.0).real(n0, M)
+    want = comb_closed_form_dyadic(fs, fc, num, den.bit_length() - 1, amp, td, n0, M)
+    with oracle.mutation(code):
+        T = oracle.direct_any(x, "f64", n0, fs, fc, fo)
+    assert rel(T, want) > 1e-3
