@@ -461,6 +461,34 @@ int pcal_rotfold_finalize(pcal_rotfold* r, double* phasors_out, void* stream);
 /* The FP32 accumulators, float [lanes][N][4] = (sum re, sum im, compensation re, compensation im). */
 int pcal_rotfold_get_acc(pcal_rotfold* r, float* host_out);
 
+/*
+ * ---- Long-period plans: offsets that cannot be folded -----------------------
+ *
+ * For a comb offset whose combined period L (Eq. 4) is beyond PCAL_MAX_L (a
+ * prime offset) or that is not a whole number of hertz, pcal_rotplan_* rotates
+ * every sample (Eq. 3) into N bins (Eq. 2) in double-float: per thread a
+ * rotator advanced by one complex multiplication per sample and re-seeded
+ * every 256 samples from the exact phase frac(n*f_offset/fs) (double-double,
+ * FP64 sincospi); then the DFT, the products and the post-processing of the
+ * folded path.  fs and f_comb integral Hz, N = fs/f_comb <= PCAL_BATCH_MAX_N,
+ * 0 <= f_offset < f_comb any value; f32, int8 or 2-bit samples; at most 2^52
+ * samples per plan.  The throughput is arithmetic-bound (several times below
+ * the folded path).
+ */
+typedef struct pcal_rotplan pcal_rotplan;
+
+int pcal_rotplan_create(double fs, double f_comb, double f_offset, int N, int sample_format, pcal_rotplan** out);
+int pcal_rotplan_destroy(pcal_rotplan* plan);
+int pcal_rotplan_set_levels(pcal_rotplan* plan, const double levels[4]);
+/* samples: DEVICE, n samples continuing the absolute index; asynchronous on stream. */
+int pcal_rotplan_accumulate(pcal_rotplan* plan, const void* samples, int64_t n, void* stream);
+/* Finalize on `stream` (results stay on the device) and start the next period. */
+int pcal_rotplan_finalize_device(pcal_rotplan* plan, void* stream);
+/* Results of the last finalize (synchronises; layout as pcal_read_results and pcal_read_post;
+ * any pointer may be NULL). */
+int pcal_rotplan_read_results(pcal_rotplan* plan, double* phasors, double* amp, double* phase, double* unwrapped,
+                              double* td, double* sigma, double* td_peak, double* bandpass_phase);
+
 /* Static name of a status code. */
 const char* pcal_strerror(int code);
 

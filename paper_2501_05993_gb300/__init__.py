@@ -151,6 +151,12 @@ def load(path: str | None = None):
         "pcal_rotfold_accumulate": ([vp, vp, i64, vp], ci),
         "pcal_rotfold_finalize": ([vp, vp, vp], ci),
         "pcal_rotfold_get_acc": ([vp, vp], ci),
+        "pcal_rotplan_create": ([dbl, dbl, dbl, ci, ci, P(vp)], ci),
+        "pcal_rotplan_destroy": ([vp], ci),
+        "pcal_rotplan_set_levels": ([vp, P(dbl)], ci),
+        "pcal_rotplan_accumulate": ([vp, vp, i64, vp], ci),
+        "pcal_rotplan_finalize_device": ([vp, vp], ci),
+        "pcal_rotplan_read_results": ([vp, vp, vp, vp, vp, vp, vp, vp, vp], ci),
         "pcal_server_create": ([P(ServerConfig), P(vp)], ci),
         "pcal_server_destroy": ([vp], ci),
         "pcal_server_open": ([vp, P(ChannelDesc), P(ci)], ci),
@@ -676,3 +682,55 @@ class RotFold:
         out = np.empty(2 * self.N)
         _check(load().pcal_rotfold_finalize(self.handle, out.ctypes.data, _stream(stream)), "pcal_rotfold_finalize")
         return out[0::2] + 1j * out[1::2]
+
+
+# ---- long-period plans: offsets that cannot be folded ---------------------------------
+
+
+class RotPlan:
+    """Per-sample double-float rotation for prime or non-integral offsets."""
+
+    def __init__(self, fs, f_comb, f_offset, fmt: str = "i8", N=None):
+        self.N = int(N if N is not None else round(fs / f_comb))
+        h = ctypes.c_void_p()
+        _check(load().pcal_rotplan_create(float(fs), float(f_comb), float(f_offset), self.N, FORMATS[fmt],
+                                          ctypes.byref(h)), "pcal_rotplan_create")
+        self.handle = h.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().pcal_rotplan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def accumulate(self, samples, n: int, stream=None):
+        _check(load().pcal_rotplan_accumulate(self.handle, _ptr(samples), int(n), _stream(stream)),
+               "pcal_rotplan_accumulate")
+
+    def finalize_device(self, stream=None):
+        _check(load().pcal_rotplan_finalize_device(self.handle, _stream(stream)), "pcal_rotplan_finalize_device")
+
+    def results(self) -> dict:
+        N = self.N
+        ph, amp, phase, unw, bp = np.empty(2 * N), np.empty(N), np.empty(N), np.empty(N), np.empty(N)
+        td, sig, tp = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(load().pcal_rotplan_read_results(self.handle, ph.ctypes.data, amp.ctypes.data, phase.ctypes.data,
+                                                unw.ctypes.data, ctypes.addressof(td), ctypes.addressof(sig),
+                                                ctypes.addressof(tp), bp.ctypes.data), "pcal_rotplan_read_results")
+        return {"phasors": ph[0::2] + 1j * ph[1::2], "amp": amp, "phase": phase, "unwrapped": unw,
+                "td": td.value, "sigma_td": sig.value, "td_peak": tp.value, "bandpass_phase": bp}
+
+    def finalize(self) -> np.ndarray:
+        self.finalize_device()
+        return self.results()["phasors"]

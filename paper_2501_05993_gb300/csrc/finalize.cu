@@ -1086,7 +1086,75 @@ cudaError_t launch_cluster_finalize(const FinArgs& a, int C, cudaStream_t s) {
     return cudaLaunchKernelEx(&cfg, fin_cluster_kernel, a);
 }
 
+// Finalize of a long-period plan (one CTA): the lanes of each bin added in
+// df (lane order), then the DFT, the products and the post-processing of the
+// folded path.
+__global__ void __launch_bounds__(kClusterThreads) rot_finalize_kernel(FinArgs a, const float4* acc, int lanes) {
+    __shared__ float4 part[kClusterThreads];
+    extern __shared__ __align__(16) uint8_t dsm[];
+    const int N = (int)a.N;
+    const ClusterSmem sm = cluster_layout(dsm, N);
+    const int t = threadIdx.x;
+    for (int i = t; i < N; i += blockDim.x) sm.sTw[i] = a.twN[i];
+    // bin b: its lanes split over G threads, then the G partials in order
+    const int G = (int)blockDim.x / N > 0 ? (int)blockDim.x / N : 1;
+    const int per_round = (int)blockDim.x / G;
+    for (int b0 = 0; b0 < N; b0 += per_round) {
+        const int b = b0 + t / G, g = t % G;
+        df sr{0.f, 0.f}, si{0.f, 0.f};
+        if (t / G < per_round && b < N)
+            for (int l = g; l < lanes; l += G) {
+                const float4 v = acc[(int64_t)l * N + b];
+                sr = pcal_df::add(sr, df{v.x, v.y});
+                si = pcal_df::add(si, df{v.z, v.w});
+            }
+        part[t] = make_float4(sr.hi, sr.lo, si.hi, si.lo);
+        __syncthreads();
+        if (g == 0 && t / G < per_round && b < N) {
+            df tr{0.f, 0.f}, ti{0.f, 0.f};
+            for (int q = 0; q < G; ++q) {
+                const float4 v = part[t + q];
+                tr = pcal_df::add(tr, df{v.x, v.y});
+                ti = pcal_df::add(ti, df{v.z, v.w});
+            }
+            sm.sP[b] = make_float2(tr.hi + tr.lo, ti.hi + ti.lo);
+        }
+        __syncthreads();
+    }
+    dft_range(sm.sP, sm.sTw, N, 0, N, sm.sT);
+    __syncthreads();
+    if (t < 32) tone_products_warp(a, sm.sT, sm.pm);
+    else if (t < 64) peak_delay_warp(a, sm.sP);
+    __syncthreads();
+    write_results_block(a, sm.sT, sm.pm);
+}
+
 }  // namespace
+
+cudaError_t launch_rot_finalize(const float4* acc, int lanes, int N, double fs, double fc, int64_t M,
+                                const float2* twN, double* res, cudaStream_t s) {
+    FinArgs a{};
+    a.N = N;
+    a.L = N;
+    a.fs_hz = fs;
+    a.M = (double)M;
+    a.two_over_m = M > 0 ? (float)(2.0 / (double)M) : 0.0f;
+    const double tpf = 6.283185307179586476925 * fc;
+    a.two_pi_fc.hi = (float)tpf;
+    a.two_pi_fc.lo = (float)(tpf - (double)a.two_pi_fc.hi);
+    a.twN = twN;
+    a.res = res;
+    a.extra = res + 5 * (int64_t)N + 3;
+    static bool attr_set = false;
+    if (!attr_set) {
+        const cudaError_t e = cudaFuncSetAttribute(rot_finalize_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)cluster_smem_bytes(kClusterBigN));
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    rot_finalize_kernel<<<1, kClusterThreads, cluster_smem_bytes(N), s>>>(a, acc, lanes);
+    return cudaGetLastError();
+}
 
 cudaError_t prepare_batch_finalize() {
     const int C = cluster_size_for_device();

@@ -171,6 +171,9 @@ struct BatchPiece {
 };
 
 cudaError_t prepare_batch_finalize();
+// Finalize of a long-period plan: acc = [lanes][N] double-float bin sums.
+cudaError_t launch_rot_finalize(const float4* acc, int lanes, int N, double fs, double fc, int64_t M,
+                                const float2* twN, double* res, cudaStream_t s);
 // Finalize channels list[i] (or i when list is null), i < n, with one cluster each.
 cudaError_t launch_batch_finalize(BatchChan* d_ch, int n, int max_n, const int* d_list, cudaStream_t s);
 
