@@ -489,6 +489,16 @@ int pcal_rotplan_finalize_device(pcal_rotplan* plan, void* stream);
 int pcal_rotplan_read_results(pcal_rotplan* plan, double* phasors, double* amp, double* phase, double* unwrapped,
                               double* td, double* sigma, double* td_peak, double* bandpass_phase);
 
+/*
+ * Failure detection without a fault: one block waits, with the bounded
+ * mbarrier wait every TMA-fed kernel uses, on a phase nothing completes, for
+ * limit_s seconds (0 < limit_s <= 2), records that it gave up and returns
+ * normally.  Returns PCAL_ETIMEOUT with *flags_out = the device error bits
+ * (the expected outcome: the context stays usable), PCAL_OK if nothing gave
+ * up.  Synchronous; for tests and diagnostics.
+ */
+int pcal_selftest_wait_timeout(double limit_s, unsigned int* flags_out);
+
 /* Static name of a status code. */
 const char* pcal_strerror(int code);
 

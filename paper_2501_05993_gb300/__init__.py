@@ -151,6 +151,7 @@ def load(path: str | None = None):
         "pcal_rotfold_accumulate": ([vp, vp, i64, vp], ci),
         "pcal_rotfold_finalize": ([vp, vp, vp], ci),
         "pcal_rotfold_get_acc": ([vp, vp], ci),
+        "pcal_selftest_wait_timeout": ([dbl, P(ctypes.c_uint)], ci),
         "pcal_rotplan_create": ([dbl, dbl, dbl, ci, ci, P(vp)], ci),
         "pcal_rotplan_destroy": ([vp], ci),
         "pcal_rotplan_set_levels": ([vp, P(dbl)], ci),
@@ -734,3 +735,10 @@ class RotPlan:
     def finalize(self) -> np.ndarray:
         self.finalize_device()
         return self.results()["phasors"]
+
+
+def pcal_selftest_wait_timeout(limit_s: float) -> tuple[int, int]:
+    """(status, device error bits) of a bounded wait that is made to run out."""
+    flags = ctypes.c_uint()
+    rc = load().pcal_selftest_wait_timeout(float(limit_s), ctypes.byref(flags))
+    return rc, flags.value

@@ -8,6 +8,7 @@
 // thread per bin in sample order, so they are deterministic.
 #include "df64.cuh"
 #include "internal.cuh"
+#include "ptx.cuh"
 
 namespace {
 
@@ -84,6 +85,21 @@ __global__ void export2_kernel(const unsigned long long* __restrict__ acc, const
     }
 }
 
+// Failure detection without a fault: every thread of one block waits on an
+// mbarrier phase that nothing completes, with the bounded wait of the fold
+// kernels and a short limit; each thread that gives up sets a bit, and the
+// block then returns normally.
+__global__ void wait_timeout_kernel(uint64_t limit_ns, unsigned int* flags) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        pcal_ptx::mbar_init(&bar, (1u << 20) - 1);  // the largest count: more arrivals than will come
+        pcal_ptx::fence_barrier_init();
+    }
+    __syncthreads();
+    if (!pcal_ptx::mbar_wait(&bar, 0, limit_ns)) atomicOr(flags, PCAL_DERR_FULL_WAIT);
+    __syncthreads();
+}
+
 inline int grid_for(int64_t work, int threads, int num_sms) {
     int64_t g = (work + threads - 1) / threads;
     int64_t cap = (int64_t)num_sms * 8;
@@ -131,4 +147,23 @@ cudaError_t launch_export_bins(pcal_plan* p, void* d_out, cudaStream_t s) {
                                                                   reinterpret_cast<long long*>(d_out));
     p->stats.kernel_launches += 1;
     return cudaGetLastError();
+}
+
+extern "C" int pcal_selftest_wait_timeout(double limit_s, unsigned int* flags_out) {
+    if (!flags_out || !(limit_s > 0.0) || limit_s > 2.0) return PCAL_EINVAL;
+    unsigned int* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(d, 0, sizeof(unsigned int));
+    if (e == cudaSuccess) {
+        wait_timeout_kernel<<<1, 64>>>((uint64_t)(limit_s * 1e9), d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(flags_out, d, sizeof(unsigned int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return PCAL_ECUDA;
+    }
+    return *flags_out ? PCAL_ETIMEOUT : PCAL_OK;
 }

@@ -286,3 +286,22 @@ def test_full_size_f32_c1(pcal):
     pr = oracle.products(ref, n, fs, fc, fo)
     assert abs(r["td"] - pr["td"]) <= 1e-3 * pr["sigma_td"]
     assert abs(r["td"] - td) < 5 * pr["sigma_td"]  # unquantised data: no bias
+
+
+def test_bounded_wait_runs_out_and_the_context_survives(pcal):
+    """A wait on a phase nothing completes gives up after its limit, the
+    kernel reports it through the error bits and returns, and the device
+    keeps working (a plan runs right after)."""
+    import time
+
+    t0 = time.perf_counter()
+    rc, flags = pcal.pcal_selftest_wait_timeout(0.05)
+    dt = time.perf_counter() - t0
+    assert rc == pcal.PCAL_ETIMEOUT and flags & 1
+    assert dt < 5.0
+    fs, fc, fo = PLANS["c1"]
+    host = synth.Stream(fs=fs, fc=fc, fo=fo, amp=0.1, td=1e-9, seed=2).bits2(0, 4 * 40_000)
+    with pcal.Plan(fs, fc, fo, "2bit") as p:
+        keep, addr = to_dev(host, 1)
+        p.accumulate(addr, 4 * 40_000)
+        assert np.array_equal(p.bins(), oracle.counts_2bit(host, 0, p.L))
