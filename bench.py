@@ -188,6 +188,48 @@ def cpu_oracle_rate(sample_samples: int):
     return sample_samples / dt / 1e9, dt
 
 
+def _fold_counts_slice(job):
+    """One worker of the all-core CPU fold: exact per-code counts of its slice."""
+    import oracle
+    import synth
+
+    n0, count, L = job
+    s = synth.Stream(fs=FS, fc=FC, fo=FO, amp=AMP, td=TD, seed=SEED)
+    host = s.bits2(n0, count)
+    t0 = time.perf_counter()
+    c = oracle.counts_2bit(host, n0, L)
+    return c, time.perf_counter() - t0
+
+
+def cpu_fold_rates(sample: int):
+    """The oracle's fold-first route on the host (exact per-code counts, FP64
+    decode and tones): single-threaded, and on every core with one spawned
+    process per core folding its own slice (the slices' counts add exactly).
+    Returns (single-core Gsamples/s, all-core Gsamples/s, cores)."""
+    import multiprocessing as mp
+
+    import oracle
+
+    L = oracle.plan(FS, FC, FO)["L"]
+    sample = sample // 64 * 64
+    c1, dt1 = _fold_counts_slice((0, sample, L))
+    t0 = time.perf_counter()
+    oracle.tones_from_bins(oracle.decode_counts(c1), FS, FC, FO)
+    dt1 += time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    per = sample // cores // 64 * 64
+    jobs = [(k * per, per, L) for k in range(cores)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_fold_counts_slice, [(0, 64, L)] * cores)  # workers import and warm up
+        parts = pool.map(_fold_counts_slice, jobs)
+    # the slices fold at the same time: the slowest fold, then the combine
+    t0 = time.perf_counter()
+    total = sum(c for c, _ in parts)
+    oracle.tones_from_bins(oracle.decode_counts(total), FS, FC, FO)
+    dtn = max(dt for _, dt in parts) + (time.perf_counter() - t0)
+    return sample / dt1 / 1e9, per * cores / dtn / 1e9, cores
+
+
 def run_reference(args):
     rank, world, _ = rank_env()
     if rank != 0:
@@ -337,10 +379,19 @@ def run_gpu(args):
                 "kernel": "bulk_fold_kernel<2-bit>", "algorithmic_bytes_per_launch": nbytes}
 
     cpu = None
+    cpu_fold = None
     if rank == 0 and not args.no_cpu_baseline:
         v, dt = cpu_oracle_rate(args.cpu_sample)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"direct FP64 definition over the first {args.cpu_sample} samples ({dt:.1f} s)"}
+        try:
+            one, alln, cores = cpu_fold_rates(M)
+            cpu_fold = {"value_1core": one, "value_allcore": alln, "unit": UNIT, "cores": cores, "kind": "oracle fold",
+                        "sample": f"the oracle's fold-first route (exact per-code counts, FP64 decode and tones) "
+                                  f"over {M} samples; all cores: one spawned process per core folds its slice "
+                                  f"(time = slowest slice + the combine)"}
+        except Exception as e:
+            cpu_fold = {"error": f"{type(e).__name__}: {e}"[:200]}
 
     plan.close()
     if rank == 0:
@@ -353,7 +404,8 @@ def run_gpu(args):
                        "fold_ms": fold_ms, "finalize_ms": fin_ms, "fold_launches_per_step": fold_launches / args.steps,
                        "kernel_timing": "fold and finalize each timed over K back-to-back launches after the timed region", "td_s": res["td"], "sigma_td_s": res["sigma_td"],
                        "td_injected_s": TD},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
+            "roofline": roofline, "cpu_baseline": cpu, "cpu_fold_baseline": cpu_fold, "e2e": e2e, "clocks": clk,
+            "gpu_launches": launches,
         }
         if world == 1 and not args.no_extras:
             # the other parts of the headline metric: batched vs plain, serving latency
