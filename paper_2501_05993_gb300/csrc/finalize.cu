@@ -301,17 +301,18 @@ __device__ void peak_delay_warp(const FinArgs& a, const float2* P) {
         }
     }
     if (lane == 0) {
+        // FP32 throughout (a position to ~1e-5 bin): scalar FP64 square roots
+        // and divisions are long dependent chains on GB300's FP64 pipe
         const float2 zm = P[(bi + N - 1) % N], zp = P[(bi + 1) % N];
-        const double ym = sqrt((double)zm.x * zm.x + (double)zm.y * zm.y);
-        const double y0 = sqrt((double)best);
-        const double yp = sqrt((double)zp.x * zp.x + (double)zp.y * zp.y);
-        const double den = ym - 2.0 * y0 + yp;
-        const double pos = bi + (den != 0.0 ? 0.5 * (ym - yp) / den : 0.0);
-        const double half = (double)N / (2.0 * a.fs_hz);
-        double t = -pos / a.fs_hz + half;
-        t -= floor(t / (2.0 * half)) * (2.0 * half);
-        a.extra[0] = best > 0.f ? t - half : __longlong_as_double(0x7ff8000000000000ll);
-        a.extra[1] = pos;
+        const float ym = sqrtf(zm.x * zm.x + zm.y * zm.y), y0 = sqrtf(best);
+        const float yp = sqrtf(zp.x * zp.x + zp.y * zp.y);
+        const float den = ym - 2.f * y0 + yp;
+        const float pos = (float)bi + (den != 0.f ? 0.5f * (ym - yp) / den : 0.f);
+        // -pos wrapped into [-N/2, N/2) bins, then seconds
+        float q = -pos;
+        q -= (float)N * floorf((q + 0.5f * (float)N) / (float)N);
+        a.extra[0] = best > 0.f ? (double)(q / (float)a.fs_hz) : __longlong_as_double(0x7ff8000000000000ll);
+        a.extra[1] = (double)pos;
     }
 }
 
@@ -553,7 +554,10 @@ __device__ inline ClusterSmem cluster_layout(uint8_t* base, int64_t N) {
 // The products of tone_products, by one warp with no block barrier: lane l
 // takes the contiguous tones [l*c, l*c + c), c = ceil(N/32).  Loops over a
 // lane's tones are not unrolled, for the reason given at warp_sums_df.
-__device__ __noinline__ void tone_products_warp(const FinArgs& a, const float2* sT, const WarpProductsSmem& m) {
+__device__ __noinline__ void tone_products_warp(const FinArgs& a, const float2* __restrict__ sT,
+                                                float* __restrict__ psi, float* __restrict__ wt,
+                                                float2* __restrict__ un, float2* __restrict__ out) {
+    double* const extra = a.extra;
     const int N = (int)a.N;
     const int lane = threadIdx.x & 31;
     const int c = (N + 31) / 32;
@@ -563,30 +567,30 @@ __device__ __noinline__ void tone_products_warp(const FinArgs& a, const float2* 
 #pragma unroll 1
     for (int i = i0; i < i1; ++i) {
         const float2 z = sT[i];
-        m.psi[i] = wrap_pi_f(atan2f(z.y, z.x) + 1.5707963267948966f);
-        m.w[i] = z.x * z.x + z.y * z.y;
+        psi[i] = wrap_pi_f(atan2f(z.y, z.x) + 1.5707963267948966f);
+        wt[i] = z.x * z.x + z.y * z.y;
     }
     __syncwarp();
     // 2. unwrap: u_i = psi_0 + sum_{j=1..i} wrap(psi_j - psi_{j-1}), df sums
     const int j0 = i0 > 1 ? i0 : 1;
     df local{0.f, 0.f};
 #pragma unroll 1
-    for (int i = j0; i < i1; ++i) local = pcal_df::add_f(local, wrap_pi_f(m.psi[i] - m.psi[i - 1]));
-    df run = pcal_df::add_f(warp_exclusive_scan_df(local), m.psi[0]);
+    for (int i = j0; i < i1; ++i) local = pcal_df::add_f(local, wrap_pi_f(psi[i] - psi[i - 1]));
+    df run = pcal_df::add_f(warp_exclusive_scan_df(local), psi[0]);
 #pragma unroll 1
     for (int i = i0; i < i1; ++i) {
-        if (i > 0) run = pcal_df::add_f(run, wrap_pi_f(m.psi[i] - m.psi[i - 1]));
-        m.un[i] = make_float2(run.hi, run.lo);
+        if (i > 0) run = pcal_df::add_f(run, wrap_pi_f(psi[i] - psi[i - 1]));
+        un[i] = make_float2(run.hi, run.lo);
     }
     // 3. weighted least squares of u_i against the tone index x_i = i (the
     //    frequency is f_i = f_comb*i + f_offset), weights w_i = |T_i|^2
     df s3[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
 #pragma unroll 1
     for (int i = i0; i < i1; ++i) {
-        const float w = m.w[i];
+        const float w = wt[i];
         s3[0] = pcal_df::add_f(s3[0], w);
         s3[1] = pcal_df::add(s3[1], pcal_df::two_prod(w, (float)i));
-        s3[2] = pcal_df::add(s3[2], pcal_df::mul_f(df{m.un[i].x, m.un[i].y}, w));
+        s3[2] = pcal_df::add(s3[2], pcal_df::mul_f(df{un[i].x, un[i].y}, w));
     }
     warp_sums_df<3>(s3);
     const df W = s3[0];
@@ -600,9 +604,9 @@ __device__ __noinline__ void tone_products_warp(const FinArgs& a, const float2* 
         df s2[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
 #pragma unroll 1
         for (int i = i0; i < i1; ++i) {
-            const float w = m.w[i];
+            const float w = wt[i];
             const df dx = pcal_df::sub(df{(float)i, 0.f}, xbar);
-            const df du = pcal_df::sub(df{m.un[i].x, m.un[i].y}, ubar);
+            const df du = pcal_df::sub(df{un[i].x, un[i].y}, ubar);
             const df wdx = pcal_df::mul_f(dx, w);
             s2[0] = pcal_df::add(s2[0], pcal_df::mul(wdx, dx));
             s2[1] = pcal_df::add(s2[1], pcal_df::mul(wdx, du));
@@ -622,16 +626,16 @@ __device__ __noinline__ void tone_products_warp(const FinArgs& a, const float2* 
         }
     }
     if (lane == 0) {
-        m.out[0] = make_float2(td.hi, td.lo);
-        m.out[1] = make_float2(sig.hi, sig.lo);
+        out[0] = make_float2(td.hi, td.lo);
+        out[1] = make_float2(sig.hi, sig.lo);
     }
-    if (a.extra) {
+    if (extra) {
         // bandpass phase with the fitted delay removed: u_i - ubar - slope*(i - xbar)
 #pragma unroll 1
         for (int i = i0; i < i1; ++i) {
-            const df r = pcal_df::sub(pcal_df::sub(df{m.un[i].x, m.un[i].y}, ubar),
+            const df r = pcal_df::sub(pcal_df::sub(df{un[i].x, un[i].y}, ubar),
                                       pcal_df::mul(slope, pcal_df::sub(df{(float)i, 0.f}, xbar)));
-            a.extra[2 + i] = fitted ? (double)r.hi + (double)r.lo : __longlong_as_double(0x7ff8000000000000ll);
+            extra[2 + i] = fitted ? (double)r.hi + (double)r.lo : __longlong_as_double(0x7ff8000000000000ll);
         }
     }
 }
@@ -859,7 +863,7 @@ __device__ __forceinline__ bool cluster_finalize(const FinArgs& a) {
         if (r != 0) return false;
     }
     __syncthreads();
-    if (t < 32) tone_products_warp(a, sT, sm.pm);
+    if (t < 32) tone_products_warp(a, sT, sm.pm.psi, sm.pm.w, sm.pm.un, sm.pm.out);
     else if (t < 64 && a.extra) peak_delay_warp(a, sP);
     __syncthreads();
     write_results_block(a, sT, sm.pm);
@@ -1123,7 +1127,7 @@ __global__ void __launch_bounds__(kClusterThreads) rot_finalize_kernel(FinArgs a
     }
     dft_range(sm.sP, sm.sTw, N, 0, N, sm.sT);
     __syncthreads();
-    if (t < 32) tone_products_warp(a, sm.sT, sm.pm);
+    if (t < 32) tone_products_warp(a, sm.sT, sm.pm.psi, sm.pm.w, sm.pm.un, sm.pm.out);
     else if (t < 64) peak_delay_warp(a, sm.sP);
     __syncthreads();
     write_results_block(a, sm.sT, sm.pm);
