@@ -301,6 +301,26 @@ def test_delay_recovery_two_bit():
     assert abs(pr["td"] - td) < 5 * pr["sigma_td"]
 
 
+def test_phase_residuals_chi_square_c1():
+    """Per-tone phase residuals after the delay fit are consistent with the
+    expected phase noise: for a tone of amplitude A in unit noise over M
+    samples, sigma_phi = sqrt(2/M)/A, so sum(resid^2)/sigma_phi^2 over the N
+    tones follows chi^2 with N - 2 degrees of freedom.  Checked over several
+    seeds (bounds hold with probability > 0.999 each)."""
+    fs, fc, fo, amp, td, M = 16_000_000, 1_000_000, 10_000, 0.02, 3.7e-9, 4_000_000
+    N = fs // fc
+    sigma_phi = math.sqrt(2.0 / M) / amp
+    stats = []
+    for seed in range(5):
+        x = synth.Stream(fs=fs, fc=fc, fo=fo, amp=amp, td=td, seed=9100 + seed).f32(0, M)
+        pr = oracle.products(oracle.fold(x, "f32", 0, fs, fc, fo), M, fs, fc, fo)
+        stats.append(float(np.sum((pr["bandpass_phase"] / sigma_phi) ** 2)))
+    dof = N - 2
+    for chi2 in stats:
+        assert 0.15 * dof < chi2 < 3.0 * dof, stats
+    assert 0.5 * dof < np.mean(stats) < 1.6 * dof, stats
+
+
 # ---------------------------------------------------------- planted mistakes
 
 def _pin_battery():
