@@ -379,10 +379,17 @@ __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_co
         // kernels back; waiting for the preceding kernel here (it waited for
         // its own predecessor) orders these atomics after that clearing.
         grid_dependency_wait();
-        // one atomic per (column, sample): consecutive threads, consecutive bins
+        // one atomic per (column, sample): consecutive threads, consecutive
+        // bins; each row group starts at its own offset, so that the CTAs
+        // flushing at the same time spread over the bins.  bin = (k_a + 16 gc
+        // + j) mod L = (base + t) mod L with base + t < L + 2^12 (L <= 2^20).
         const int S = a.merge_stride;
         const int tasks = a.col_width * 16;
-        for (int t = tid; t < tasks; t += blockDim.x) {
+        const uint32_t Lu = (uint32_t)a.L;
+        const uint32_t base = (uint32_t)((a.k_a + 16 * (int64_t)c0) % a.L);
+        const int rot = (int)(rg * tasks / a.row_groups);  // rg < row_groups
+        for (int t0 = tid; t0 < tasks; t0 += blockDim.x) {
+            const int t = t0 + rot < tasks ? t0 + rot : t0 + rot - tasks;
             const int cl = t >> 4, j = t & 15;
             const int gc = c0 + cl;
             if (gc >= a.cols_total) continue;
@@ -392,7 +399,9 @@ __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_co
             const uint32_t shl = ((m[(16 + (pl & 15)) * S + cl] >> (16 * (pl >> 4))) & 0xFFFFu) +
                                  ((m[(16 + (ph & 15)) * S + cl] >> (16 * (ph >> 4))) & 0xFFFFu);
             if ((sl | sh) == 0) continue;
-            const int64_t bin = (a.k_a + 16 * (int64_t)gc + j) % a.L;
+            uint32_t bin = base + (uint32_t)t;
+            if (bin >= Lu) bin -= Lu;
+            if (bin >= Lu) bin %= Lu;
             atomicAdd(&a.acc2[bin], (unsigned long long)sl | ((unsigned long long)sh << 21) |
                                          ((unsigned long long)shl << 42));
         }
@@ -409,12 +418,19 @@ __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_co
         }
         __syncthreads();
         grid_dependency_wait();  // as for the 2-bit flush
-        for (int t = tid; t < a.col_width * 4; t += blockDim.x) {
+        const int tasks = a.col_width * 4;
+        const uint32_t Lu = (uint32_t)a.L;
+        const uint32_t base = (uint32_t)((a.k_a + 4 * (int64_t)c0) % a.L);
+        const int rot = (int)(rg * tasks / a.row_groups);  // rg < row_groups
+        for (int t0 = tid; t0 < tasks; t0 += blockDim.x) {
+            const int t = t0 + rot < tasks ? t0 + rot : t0 + rot - tasks;
             const int cl = t >> 2, j = t & 3;
             const int gc = c0 + cl;
             const int v = m[j * S + cl];
             if (gc >= a.cols_total || v == 0) continue;
-            const int64_t bin = (a.k_a + 4 * (int64_t)gc + j) % a.L;
+            uint32_t bin = base + (uint32_t)t;
+            if (bin >= Lu) bin -= Lu;
+            if (bin >= Lu) bin %= Lu;
             atomicAdd(reinterpret_cast<unsigned long long*>(&a.acc8[bin]), (unsigned long long)(long long)v);
         }
     } else {

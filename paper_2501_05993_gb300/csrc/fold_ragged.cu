@@ -6,14 +6,27 @@
 // and inputs too short for the bulk kernel.  2-bit and int8 bins are exact
 // integers, so atomic order does not matter; float32 bins are summed by one
 // thread per bin in sample order, so they are deterministic.
+//
+// Every kernel that touches the bins here is launched as a programmatic
+// dependent of the kernel before it: it lets its own successor start
+// launching at once, then waits for its predecessor (whose adds, or the
+// finalize's clearing, come first) before it touches the bins.  The stream's
+// kernels therefore still complete in launch order, while their launches
+// overlap.
 #include "df64.cuh"
 #include "internal.cuh"
 #include "ptx.cuh"
 
 namespace {
 
+__device__ __forceinline__ void chain_in() {
+    pcal_ptx::allow_dependents();
+    pcal_ptx::grid_dependency_wait();
+}
+
 __global__ void ragged_2bit_kernel(const uint8_t* __restrict__ bytes, int64_t n_bytes, int64_t k0, int64_t L,
                                    unsigned long long* __restrict__ acc) {
+    chain_in();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_bytes;
          i += (int64_t)gridDim.x * blockDim.x) {
         uint32_t b = bytes[i];
@@ -33,6 +46,7 @@ __global__ void ragged_2bit_kernel(const uint8_t* __restrict__ bytes, int64_t n_
 
 __global__ void ragged_i8_kernel(const int8_t* __restrict__ x, int64_t n, int64_t k0, int64_t L,
                                  long long* __restrict__ acc) {
+    chain_in();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         int v = x[i];
         if (v) atomicAdd(reinterpret_cast<unsigned long long*>(&acc[(k0 + i) % L]), (unsigned long long)(long long)v);
@@ -43,6 +57,7 @@ __global__ void ragged_i8_kernel(const int8_t* __restrict__ x, int64_t n, int64_
 // order, in double-float, and adds the sum to the plan's double-float bin.
 __global__ void ragged_f32_kernel(const float* __restrict__ x, int64_t n, int64_t k0, int64_t L,
                                   float2* __restrict__ acc) {
+    chain_in();
     int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= L) return;
     int64_t t = (k - k0 % L + L) % L;  // first sample index of this run in bin k
@@ -57,6 +72,7 @@ __global__ void ragged_f32_kernel(const float* __restrict__ x, int64_t n, int64_
 // Move the packed 21-bit fields into the wide 64-bit arrays and clear them.
 __global__ void spill2_kernel(unsigned long long* __restrict__ acc, unsigned long long* __restrict__ wide,
                               int64_t L) {
+    chain_in();
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < L; k += (int64_t)gridDim.x * blockDim.x) {
         unsigned long long v = acc[k];
         if (v) {
@@ -100,6 +116,21 @@ __global__ void wait_timeout_kernel(uint64_t limit_ns, unsigned int* flags) {
     __syncthreads();
 }
 
+// Launch with programmatic stream serialization (see chain_in).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_chained(void (*k)(KArgs...), int grid, int block, cudaStream_t s, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, static_cast<Args&&>(args)...);
+}
+
 inline int grid_for(int64_t work, int threads, int num_sms) {
     int64_t g = (work + threads - 1) / threads;
     int64_t cap = (int64_t)num_sms * 8;
@@ -112,31 +143,32 @@ inline int grid_for(int64_t work, int threads, int num_sms) {
 cudaError_t launch_ragged(pcal_plan* p, const uint8_t* d_bytes, int64_t n, int64_t k0, cudaStream_t s) {
     const int64_t L = p->g.L;
     if (n <= 0) return cudaSuccess;
+    cudaError_t e;
     switch (p->g.format) {
         case PCAL_2BIT: {
-            int64_t nb = n / 4;
-            ragged_2bit_kernel<<<grid_for(nb, 256, p->num_sms), 256, 0, s>>>(d_bytes, nb, k0, L, cur_acc2(p));
+            const int64_t nb = n / 4;
+            e = launch_chained(ragged_2bit_kernel, grid_for(nb, 256, p->num_sms), 256, s, d_bytes, nb, k0, L,
+                               cur_acc2(p));
             break;
         }
         case PCAL_I8:
-            ragged_i8_kernel<<<grid_for(n, 256, p->num_sms), 256, 0, s>>>(reinterpret_cast<const int8_t*>(d_bytes),
-                                                                            n, k0, L, cur_acc8(p));
+            e = launch_chained(ragged_i8_kernel, grid_for(n, 256, p->num_sms), 256, s,
+                               reinterpret_cast<const int8_t*>(d_bytes), n, k0, L, cur_acc8(p));
             break;
-        default: {
-            int64_t g = (L + 255) / 256;
-            ragged_f32_kernel<<<(unsigned)g, 256, 0, s>>>(reinterpret_cast<const float*>(d_bytes), n, k0, L,
-                                                          cur_accf(p));
+        default:
+            e = launch_chained(ragged_f32_kernel, (int)((L + 255) / 256), 256, s,
+                               reinterpret_cast<const float*>(d_bytes), n, k0, L, cur_accf(p));
             break;
-        }
     }
     p->stats.kernel_launches += 1;
-    return cudaGetLastError();
+    return e;
 }
 
 cudaError_t launch_spill2(pcal_plan* p, cudaStream_t s) {
-    spill2_kernel<<<grid_for(p->g.L, 256, p->num_sms), 256, 0, s>>>(cur_acc2(p), cur_wide2(p), p->g.L);
+    const cudaError_t e =
+        launch_chained(spill2_kernel, grid_for(p->g.L, 256, p->num_sms), 256, s, cur_acc2(p), cur_wide2(p), p->g.L);
     p->stats.kernel_launches += 1;
-    return cudaGetLastError();
+    return e;
 }
 
 cudaError_t launch_export_bins(pcal_plan* p, void* d_out, cudaStream_t s) {
