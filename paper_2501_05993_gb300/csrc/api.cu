@@ -43,6 +43,7 @@ void free_plan(pcal_plan* p) {
     }
     if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
     if (p->h_res) cudaFreeHost(p->h_res);
+    if (p->h_hint) cudaFreeHost(p->h_hint);
     delete p;
 }
 
@@ -137,6 +138,12 @@ extern "C" int pcal_plan_create(double fs, double f_comb, double f_offset, int N
     if (e == cudaSuccess) e = dalloc(&p->d_err, 4);
     if (e == cudaSuccess) e = dalloc(&p->d_sched, kSchedCounters);
     if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&p->h_res), (6 * Nn + 5) * sizeof(double));
+    if (e == cudaSuccess)
+        e = cudaHostAlloc(reinterpret_cast<void**>(&p->h_hint), kHintRing * sizeof(PrefetchHint), cudaHostAllocMapped);
+    if (e == cudaSuccess) {
+        memset(static_cast<void*>(p->h_hint), 0, kHintRing * sizeof(PrefetchHint));
+        e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&p->d_hint), p->h_hint, 0);
+    }
     if (e == cudaSuccess) e = launch_init_twiddles(p, 0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(0);
     if (e != cudaSuccess) {

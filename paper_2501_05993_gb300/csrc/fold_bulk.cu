@@ -67,9 +67,33 @@ struct BulkArgs {
     long long* acc8;
     float2* partf;    // f32: [row group][cols_total] partial sums
     unsigned int* err;
+    const PrefetchHint* hint;   // the plan's hint ring (launch epoch + 1 is the next launch)
 };
 
 using namespace pcal_ptx;
+
+// Pull the first rows of the next launch's row groups rg, rg + row_groups,
+// ... into L2, from the ring record of epoch + 1 loaded at the start (w0-w2);
+// nothing unless all three words carry that launch's tag.  Rows stay inside
+// that launch's input.
+__device__ __noinline__ void prefetch_next_launch(const BulkArgs& a, int64_t rg, unsigned long long w0,
+                                                  unsigned long long w1, unsigned long long w2) {
+    const unsigned long long tag = hint_tag((unsigned long long)a.epoch + 1ull);
+    if ((w0 >> 48) != tag || (w1 >> 48) != tag || (w2 >> 48) != tag) return;
+    constexpr unsigned long long kLow48 = (1ull << 48) - 1, kPiece = 32768;
+    const unsigned long long n_rows = w0 & kLow48, base = (w1 & kLow48) << 4;
+    const unsigned long long groups = (w2 >> 32) & 0xffffu, group_rows = (w2 >> 16) & 0xffffu,
+                             first_rows = w2 & 0xffffu;
+    const unsigned long long row_bytes = 4ull * (unsigned long long)a.cols_total;
+    for (unsigned long long r2 = (unsigned long long)rg; r2 < groups; r2 += (unsigned long long)a.row_groups) {
+        const unsigned long long row0 = r2 * group_rows;
+        if (row0 >= n_rows) break;
+        const unsigned long long rows = first_rows < n_rows - row0 ? first_rows : n_rows - row0;
+        const unsigned long long addr = base + row0 * row_bytes, bytes = rows * row_bytes;
+        for (unsigned long long off = 0; off < bytes; off += kPiece)
+            prefetch_l2(addr + off, (uint32_t)(bytes - off < kPiece ? bytes - off : kPiece));
+    }
+}
 
 // ---- per-format consumer state --------------------------------------------------
 
@@ -188,6 +212,15 @@ __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_co
         // then chunks from the column group's counter until the work or the
         // per-CTA cap runs out.  Local box j goes to stage j % stages.
         if (tid % 32 == 0) {
+            // the next launch's read start (used at the end; loaded now so
+            // that the latency of host memory hides behind the first copies)
+            unsigned long long hint0 = 0, hint1 = 0, hint2 = 0;
+            if (a.hint && cg == 0) {
+                const PrefetchHint* h = a.hint + (((unsigned long long)a.epoch + 1ull) % kHintRing);
+                hint0 = ld_relaxed_sys(&h->rows);
+                hint1 = ld_relaxed_sys(&h->base);
+                hint2 = ld_relaxed_sys(&h->groups);
+            }
             int j = 0;
             bool ok = true;
             auto stage_free = [&](int jj) -> bool {
@@ -242,6 +275,12 @@ __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_co
                     mbar_arrive(&full[jq % a.stages]);
                 }
             }
+            // This CTA grabs no more boxes: once every CTA is here the next
+            // launch may start (its CTAs take the SMs as this launch's CTAs
+            // leave, and the shared counters are free for its new epoch).
+            // The consumers still have the stages in flight to fold.
+            allow_dependents();
+            if (a.hint && cg == 0) prefetch_next_launch(a, rg, hint0, hint1, hint2);
         }
     } else {
         // ---------------- consumers ----------------
@@ -281,9 +320,10 @@ __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_co
         }
     }
     __syncthreads();
-    // Every grab of this CTA is done: the next launch in the stream may start
-    // (a finalize waits for this kernel; a fold uses a new counter epoch and
-    // adds into the same bins with atomics, or into the other bin set).
+    // Every grab of this CTA is done (the producer signalled it already): the
+    // next launch in the stream may start (a finalize waits for this kernel;
+    // a fold uses a new counter epoch and adds into the same bins with
+    // atomics, or into the other bin set).
     allow_dependents();
     if (s_failed) {
         // Drain: TMA fills whose phase no consumer waited for must land
@@ -621,6 +661,20 @@ int bulk_tiling(const pcal_plan* p, int64_t n_rows, BulkTiling* t) {
     return 0;
 }
 
+namespace {
+
+// A launch that failed to enqueue takes its published read start back: the
+// launch before it must not pull rows of a buffer nothing will read.
+void unpublish_hint(pcal_plan* p, unsigned int epoch) {
+    if (!p->h_hint) return;
+    PrefetchHint* h = p->h_hint + (epoch % kHintRing);
+    __atomic_store_n(&h->rows, 0ull, __ATOMIC_RELAXED);
+    __atomic_store_n(&h->base, 0ull, __ATOMIC_RELAXED);
+    __atomic_store_n(&h->groups, 0ull, __ATOMIC_RELAXED);
+}
+
+}  // namespace
+
 cudaError_t launch_bulk(pcal_plan* p, const void* d_rows, int64_t n_rows, int64_t k_a, cudaStream_t s, int* launched) {
     *launched = 0;
     const BulkMapEntry* hit = nullptr;
@@ -675,6 +729,24 @@ cudaError_t launch_bulk(pcal_plan* p, const void* d_rows, int64_t n_rows, int64_
     a.acc2 = cur_acc2(p);
     a.acc8 = cur_acc8(p);
     a.err = p->d_err;
+    a.hint = p->d_hint;
+    if (p->h_hint) {
+        // publish where this launch starts reading (ring slot of its epoch);
+        // a launch whose fields do not fit the packed words publishes nothing
+        const unsigned long long base = (unsigned long long)reinterpret_cast<uintptr_t>(d_rows);
+        const unsigned long long first_rows = (unsigned long long)(t.static_boxes < 4 ? t.static_boxes : 4) * t.box_rows;
+        const unsigned long long group_rows = (unsigned long long)t.static_boxes * t.box_rows;
+        if ((unsigned long long)n_rows < (1ull << 48) && base < (1ull << 52) && base % 16 == 0 &&
+            (unsigned long long)t.row_groups < (1ull << 16) && group_rows < (1ull << 16) && first_rows < (1ull << 16)) {
+            const unsigned long long tag = hint_tag(a.epoch) << 48;
+            PrefetchHint* h = p->h_hint + (a.epoch % kHintRing);
+            __atomic_store_n(&h->rows, tag | (unsigned long long)n_rows, __ATOMIC_RELAXED);
+            __atomic_store_n(&h->base, tag | (base >> 4), __ATOMIC_RELAXED);
+            __atomic_store_n(&h->groups,
+                             tag | ((unsigned long long)t.row_groups << 32) | (group_rows << 16) | first_rows,
+                             __ATOMIC_RELAXED);
+        }
+    }
     const int grid = (int)(t.col_groups * t.row_groups);
     cudaError_t e;
     if (p->g.format == PCAL_F32) {
@@ -684,12 +756,18 @@ cudaError_t launch_bulk(pcal_plan* p, const void* d_rows, int64_t n_rows, int64_
             p->d_partf = nullptr;
             p->partf_cap = 0;
             e = cudaMalloc(&p->d_partf, need * sizeof(float2));
-            if (e != cudaSuccess) return e;
+            if (e != cudaSuccess) {
+                unpublish_hint(p, a.epoch);
+                return e;
+            }
             p->partf_cap = need;
         }
         a.partf = p->d_partf;
         e = launch_one<PCAL_F32, 1>(map, a, grid, t.threads, t.smem_bytes, s);
-        if (e != cudaSuccess) return e;
+        if (e != cudaSuccess) {
+            unpublish_hint(p, a.epoch);
+            return e;
+        }
         reduce_f32_kernel<<<(unsigned)((p->g.L + 255) / 256), 256, 0, s>>>(p->d_partf, t.row_groups, t.cols_total,
                                                                            k_a, p->g.L, cur_accf(p));
         *launched = 2;
@@ -714,6 +792,8 @@ cudaError_t launch_bulk(pcal_plan* p, const void* d_rows, int64_t n_rows, int64_
     if (e == cudaSuccess) {
         *launched = 1;
         p->stats.kernel_launches += 1;
+    } else {
+        unpublish_hint(p, a.epoch);
     }
     return e;
 }

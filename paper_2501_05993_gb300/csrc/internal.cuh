@@ -55,6 +55,23 @@ constexpr int kBulkMapCache = 16;
 constexpr int kFinalizeReserveSms = 16;
 constexpr int kSchedCounters = 8192;  // dynamic box counters (one per column group) + 1
 
+// Where a plan's bulk launch with epoch e starts reading, published by the
+// host in ring slot e % kHintRing (pinned, mapped) when it enqueues that
+// launch.  The launch before it loads the slot when it starts and, once its
+// CTAs have grabbed all their work, pulls the first rows of every row group
+// into L2 while it winds down, so the next launch's first copies hit L2
+// instead of waiting for HBM.  Only a hint: a prefetch changes no result.
+// Each word carries the launch's 16-bit tag (hint_tag) in its top bits and
+// is read with one 64-bit load, so a record that is being rewritten shows
+// mismatched tags and is skipped.
+constexpr int kHintRing = 4096;
+struct PrefetchHint {
+    unsigned long long rows;    // tag << 48 | rows of the launch
+    unsigned long long base;    // tag << 48 | device address of row 0 >> 4 (rows are contiguous)
+    unsigned long long groups;  // tag << 48 | row groups << 32 | rows between their first boxes << 16 | rows to pull
+};
+__host__ __device__ inline unsigned long long hint_tag(unsigned long long epoch) { return epoch % 65535ull + 1ull; }
+
 struct pcal_plan {
     pcal_geometry g;
     double levels[4];
@@ -85,6 +102,8 @@ struct pcal_plan {
     unsigned int* d_err;          // device error flags
     unsigned long long* d_sched;  // bulk kernel box counters [kSchedCounters]: (epoch << 32) | boxes
     unsigned int bulk_epoch;      // launches of the bulk kernel (epoch of its counters)
+    PrefetchHint* h_hint;         // [kHintRing] pinned, mapped: the bulk launches' read starts
+    PrefetchHint* d_hint;         // the same ring as the kernels address it
     // host
     double* h_res;                // pinned copy of d_res
     void* h_stage[2];             // pinned staging for pcal_accumulate_host

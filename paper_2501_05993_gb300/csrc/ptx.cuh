@@ -74,6 +74,18 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
+// A load of memory another agent (the host) writes: system scope.
+__device__ __forceinline__ unsigned long long ld_relaxed_sys(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Pull `bytes` (a multiple of 16) at the 16-byte aligned global address into L2.
+__device__ __forceinline__ void prefetch_l2(unsigned long long addr, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(addr), "r"(bytes) : "memory");
+}
+
 // A tensor map that lives in global memory and was written before this
 // kernel: order that write before the tensor-map reads of the copies.
 __device__ __forceinline__ void tensormap_acquire(const CUtensorMap* map) {
