@@ -490,6 +490,39 @@ int pcal_rotplan_read_results(pcal_rotplan* plan, double* phasors, double* amp, 
                               double* td, double* sigma, double* td_peak, double* bandpass_phase);
 
 /*
+ * ---- Batched tone DFT -------------------------------------------------------
+ *
+ * T_i = sum_b P[b] e^{-j 2 pi i b / N} for C channels at once (the DFT of P of
+ * Sec. 2, after the L-to-N fold of Eq. 2).  P and T: DEVICE, C x N complex
+ * float32 (re, im interleaved, channel-major), owned by the caller; T may not
+ * alias P.  Modes:
+ *   PCAL_DFT_FP32       CUDA cores, FP32 sums
+ *   PCAL_DFT_TC_TF32X3  tensor cores (tcgen05): [Re P | Im P] . W as one real
+ *                       C x 2N x 2N contraction, operands split in two TF32
+ *                       parts, three products accumulated in FP32
+ *   PCAL_DFT_TC_BF16X3  the same with BF16 parts
+ * pcal_dft_create builds the weight tiles (2N x 2N, split, in the layout the
+ * kernel copies; 32 MB (TF32) or 16 MB (BF16) for N = 1024) once;
+ * 1 <= N <= PCAL_BATCH_MAX_N.
+ * pcal_dft_execute is asynchronous on `stream`; C <= 65535 * 128.
+ * pcal_dft_check synchronises and returns PCAL_ETIMEOUT (with the device
+ * error bits) if a bounded wait inside the kernel gave up.
+ * pcal_dft_weights_host writes the hi and lo weight tile (tile, chunk) of a
+ * tensor-core mode into host buffers of 16 KB each (rows = the tile's output
+ * columns, at most 128, returned in *rows); host-only, for tests of the layout.
+ */
+#define PCAL_DFT_FP32 0
+#define PCAL_DFT_TC_TF32X3 1
+#define PCAL_DFT_TC_BF16X3 2
+typedef struct pcal_dft pcal_dft;
+
+int pcal_dft_create(int N, int mode, pcal_dft** out);
+int pcal_dft_destroy(pcal_dft* dft);
+int pcal_dft_execute(pcal_dft* dft, const void* P, int64_t C, void* T, void* stream);
+int pcal_dft_check(pcal_dft* dft, unsigned int* flags_out);
+int pcal_dft_weights_host(int N, int mode, int tile, int chunk, void* hi, void* lo, int* rows);
+
+/*
  * Failure detection without a fault: one block waits, with the bounded
  * mbarrier wait every TMA-fed kernel uses, on a phase nothing completes, for
  * limit_s seconds (0 < limit_s <= 2), records that it gave up and returns

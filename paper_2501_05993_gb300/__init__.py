@@ -152,6 +152,11 @@ def load(path: str | None = None):
         "pcal_rotfold_finalize": ([vp, vp, vp], ci),
         "pcal_rotfold_get_acc": ([vp, vp], ci),
         "pcal_selftest_wait_timeout": ([dbl, P(ctypes.c_uint)], ci),
+        "pcal_dft_create": ([ci, ci, P(vp)], ci),
+        "pcal_dft_destroy": ([vp], ci),
+        "pcal_dft_execute": ([vp, vp, i64, vp, vp], ci),
+        "pcal_dft_check": ([vp, P(ctypes.c_uint)], ci),
+        "pcal_dft_weights_host": ([ci, ci, ci, ci, vp, vp, P(ci)], ci),
         "pcal_rotplan_create": ([dbl, dbl, dbl, ci, ci, P(vp)], ci),
         "pcal_rotplan_destroy": ([vp], ci),
         "pcal_rotplan_set_levels": ([vp, P(dbl)], ci),
@@ -735,6 +740,57 @@ class RotPlan:
     def finalize(self) -> np.ndarray:
         self.finalize_device()
         return self.results()["phasors"]
+
+
+# ---- batched tone DFT ---------------------------------------------------------------
+
+PCAL_DFT_FP32, PCAL_DFT_TC_TF32X3, PCAL_DFT_TC_BF16X3 = 0, 1, 2
+DFT_MODES = {"fp32": PCAL_DFT_FP32, "tf32x3": PCAL_DFT_TC_TF32X3, "bf16x3": PCAL_DFT_TC_BF16X3}
+
+
+class Dft:
+    """Batched N-point tone DFT of C channels: T[c, i] = sum_b P[c, b] e^{-j 2 pi i b / N}
+    (device complex64 arrays [C][N]); mode "fp32" (CUDA cores), "tf32x3" or "bf16x3" (tensor cores)."""
+
+    def __init__(self, N: int, mode: str = "tf32x3"):
+        self.N, self.mode = int(N), mode
+        h = ctypes.c_void_p()
+        _check(load().pcal_dft_create(self.N, DFT_MODES[mode], ctypes.byref(h)), "pcal_dft_create")
+        self.handle = h.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().pcal_dft_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def execute(self, P, C: int, T, stream=None):
+        _check(load().pcal_dft_execute(self.handle, _ptr(P), int(C), _ptr(T), _stream(stream)), "pcal_dft_execute")
+
+    def check(self) -> int:
+        flags = ctypes.c_uint()
+        _check(load().pcal_dft_check(self.handle, ctypes.byref(flags)), "pcal_dft_check")
+        return flags.value
+
+
+def pcal_dft_weights_host(N: int, mode: str, tile: int, chunk: int) -> tuple[np.ndarray, np.ndarray, int]:
+    """Host copy of the hi and lo weight tiles (tile, chunk) of a tensor-core mode (16 KB each)."""
+    hi, lo = np.zeros(16384, np.uint8), np.zeros(16384, np.uint8)
+    rows = ctypes.c_int()
+    _check(load().pcal_dft_weights_host(int(N), DFT_MODES[mode], int(tile), int(chunk), hi.ctypes.data,
+                                        lo.ctypes.data, ctypes.byref(rows)), "pcal_dft_weights_host")
+    return hi, lo, rows.value
 
 
 def pcal_selftest_wait_timeout(limit_s: float) -> tuple[int, int]:

@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpcal.so")
 INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["plan_geometry.cpp", "api.cu", "fold_ragged.cu", "fold_bulk.cu", "finalize.cu", "batch.cu", "serve.cu", "precision.cu", "rotplan.cu"]
+SOURCES = ["plan_geometry.cpp", "api.cu", "fold_ragged.cu", "fold_bulk.cu", "finalize.cu", "batch.cu", "serve.cu", "precision.cu", "rotplan.cu", "dft_tc.cu"]
 
 
 def nvcc() -> str:
