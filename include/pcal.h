@@ -309,6 +309,13 @@ int pcal_batch_create(const pcal_channel_desc* channels, int n_channels, pcal_ba
 int pcal_batch_destroy(pcal_batch* batch);
 int pcal_batch_get_geometry(const pcal_batch* batch, int channel, pcal_geometry* out);
 int pcal_batch_set_schedule(pcal_batch* batch, const pcal_schedule* sched);
+/* How the batch finalize runs the tone DFT (the PCAL_DFT_* modes of the
+ * batched tone DFT below): PCAL_DFT_FP32 (default) inside each channel's
+ * finalize cluster on CUDA cores; PCAL_DFT_TC_TF32X3 / PCAL_DFT_TC_BF16X3 as
+ * one tensor-core contraction per distinct N over all channels of that N (the
+ * clusters stop at P, then a products kernel finishes every channel).
+ * Synchronises the device; drops captured step graphs. */
+int pcal_batch_set_dft(pcal_batch* batch, int mode);
 int pcal_batch_get_schedule(const pcal_batch* batch, pcal_schedule* out);
 
 /*

@@ -153,6 +153,7 @@ def load(path: str | None = None):
         "pcal_rotfold_get_acc": ([vp, vp], ci),
         "pcal_selftest_wait_timeout": ([dbl, P(ctypes.c_uint)], ci),
         "pcal_dft_create": ([ci, ci, P(vp)], ci),
+        "pcal_batch_set_dft": ([vp, ci], ci),
         "pcal_dft_destroy": ([vp], ci),
         "pcal_dft_execute": ([vp, vp, i64, vp, vp], ci),
         "pcal_dft_check": ([vp, P(ctypes.c_uint)], ci),
@@ -552,6 +553,11 @@ class Batch:
         for k, v in kw.items():
             setattr(s, k, int(v))
         pcal_batch_set_schedule(self.handle, s)
+
+    def set_dft(self, mode: str):
+        """Tone DFT of the finalize: "fp32" (inside each channel's cluster), "tf32x3" or "bf16x3"
+        (one tensor-core contraction per distinct N)."""
+        _check(load().pcal_batch_set_dft(self.handle, DFT_MODES[mode]), "pcal_batch_set_dft")
 
     def autotune(self, samples, n, stream=None) -> dict:
         return pcal_batch_autotune(self.handle, samples, n, stream).as_dict()

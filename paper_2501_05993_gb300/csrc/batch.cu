@@ -476,6 +476,16 @@ struct BatchGraph {
     cudaGraphExec_t exec;
 };
 
+// Channels of one N that share a batched tone DFT: rows of P and of the
+// tones, one per channel, contiguous.
+struct DftGroup {
+    int N;
+    int count;
+    pcal_dft* dft;
+    float2* dP;
+    float2* dT;
+};
+
 struct pcal_batch {
     int n;
     int device;
@@ -500,6 +510,8 @@ struct pcal_batch {
     cudaStream_t last_stream;
     std::vector<BatchGraph> graphs;
     pcal_stats stats;
+    int dft_mode;                 // PCAL_DFT_FP32: the DFT inside each channel's cluster
+    std::vector<DftGroup> dft;    // tensor-core modes: one group per distinct N
 };
 
 int batch_shape(const pcal_schedule& sc, int cw_max, int num_sms, BatchShape* s) {
@@ -830,9 +842,103 @@ extern "C" int pcal_batch_create(const pcal_channel_desc* channels, int n_channe
     return PCAL_OK;
 }
 
+namespace {
+
+void free_dft_groups(pcal_batch* b) {
+    for (DftGroup& g : b->dft) {
+        pcal_dft_destroy(g.dft);
+        cudaFree(g.dP);
+        cudaFree(g.dT);
+    }
+    b->dft.clear();
+}
+
+// The finalize of every channel: one cluster per channel with its DFT inside,
+// or (tensor-core modes) the clusters up to P, one batched DFT per N, then the
+// products.
+cudaError_t batch_finalize_all(pcal_batch* b, cudaStream_t s, int* launches) {
+    if (b->dft_mode == PCAL_DFT_FP32) {
+        *launches = 1;
+        return launch_batch_finalize(b->d_ch, b->n, b->max_n, nullptr, s);
+    }
+    cudaError_t e = launch_batch_finalize(b->d_ch, b->n, b->max_n, nullptr, s, 1);
+    for (size_t i = 0; e == cudaSuccess && i < b->dft.size(); ++i)
+        e = launch_dft(b->dft[i].dft, b->dft[i].dP, b->dft[i].count, b->dft[i].dT, s, b->d_err);
+    if (e == cudaSuccess) e = launch_batch_products(b->d_ch, b->n, b->max_n, s);
+    *launches = 2 + (int)b->dft.size();
+    return e;
+}
+
+}  // namespace
+
+extern "C" int pcal_batch_set_dft(pcal_batch* b, int mode) {
+    if (!b) return PCAL_EINVAL;
+    if (mode != PCAL_DFT_FP32 && mode != PCAL_DFT_TC_TF32X3 && mode != PCAL_DFT_TC_BF16X3) return PCAL_EINVAL;
+    if (mode == b->dft_mode) return PCAL_OK;
+    if (cudaDeviceSynchronize() != cudaSuccess) return PCAL_ECUDA;
+    // captured steps hold the old finalize
+    for (BatchGraph& gr : b->graphs) {
+        cudaGraphExecDestroy(gr.exec);
+        cudaFree(gr.d_desc);
+        cudaFree(gr.d_ctr);
+    }
+    b->graphs.clear();
+    free_dft_groups(b);
+    for (BatchChan& c : b->h_ch) c.Pslot = c.Tslot = nullptr;
+    int rc = PCAL_OK;
+    if (mode != PCAL_DFT_FP32) {
+        for (int c = 0; c < b->n && rc == PCAL_OK; ++c) {
+            DftGroup* g = nullptr;
+            for (DftGroup& x : b->dft)
+                if (x.N == b->h_ch[c].N) g = &x;
+            if (!g) {
+                b->dft.push_back(DftGroup{b->h_ch[c].N, 0, nullptr, nullptr, nullptr});
+                g = &b->dft.back();
+                rc = pcal_dft_create(g->N, mode, &g->dft);
+            }
+            ++g->count;
+        }
+        for (DftGroup& g : b->dft) {
+            if (rc != PCAL_OK) break;
+            const size_t bytes = (size_t)g.count * g.N * sizeof(float2);
+            if (cudaMalloc(&g.dP, bytes) != cudaSuccess || cudaMalloc(&g.dT, bytes) != cudaSuccess) rc = PCAL_ENOMEM;
+            int row = 0;
+            for (BatchChan& c : b->h_ch)
+                if (rc == PCAL_OK && c.N == g.N) {
+                    c.Pslot = g.dP + (size_t)row * g.N;
+                    c.Tslot = g.dT + (size_t)row * g.N;
+                    ++row;
+                }
+        }
+    }
+    // the device copy of the channels: keep the device-side indices
+    if (rc == PCAL_OK) {
+        std::vector<BatchChan> cur(b->n);
+        if (cudaMemcpy(cur.data(), b->d_ch, sizeof(BatchChan) * b->n, cudaMemcpyDeviceToHost) != cudaSuccess)
+            rc = PCAL_ECUDA;
+        for (int c = 0; rc == PCAL_OK && c < b->n; ++c) {
+            cur[c].Pslot = b->h_ch[c].Pslot;
+            cur[c].Tslot = b->h_ch[c].Tslot;
+        }
+        if (rc == PCAL_OK &&
+            cudaMemcpy(b->d_ch, cur.data(), sizeof(BatchChan) * b->n, cudaMemcpyHostToDevice) != cudaSuccess)
+            rc = PCAL_ECUDA;
+    }
+    if (rc != PCAL_OK) {
+        free_dft_groups(b);
+        for (BatchChan& c : b->h_ch) c.Pslot = c.Tslot = nullptr;
+        b->dft_mode = PCAL_DFT_FP32;
+        (void)cudaGetLastError();
+        return rc;
+    }
+    b->dft_mode = mode;
+    return PCAL_OK;
+}
+
 extern "C" int pcal_batch_destroy(pcal_batch* b) {
     if (!b) return PCAL_OK;
     cudaDeviceSynchronize();
+    free_dft_groups(b);
     for (BatchGraph& gr : b->graphs) {
         cudaGraphExecDestroy(gr.exec);
         cudaFree(gr.d_desc);
@@ -932,9 +1038,10 @@ extern "C" int pcal_batch_accumulate(pcal_batch* b, const void* const* samples, 
 extern "C" int pcal_batch_finalize_device(pcal_batch* b, void* stream) {
     if (!b) return PCAL_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t e = launch_batch_finalize(b->d_ch, b->n, b->max_n, nullptr, s);
+    int launches = 0;
+    cudaError_t e = batch_finalize_all(b, s, &launches);
     if (e != cudaSuccess) return PCAL_ECUDA;
-    b->stats.kernel_launches += 1;
+    b->stats.kernel_launches += launches;
     b->last_stream = s;
     for (int c = 0; c < b->n; ++c) b->period_start[c] = b->n_abs[c];
     return PCAL_OK;
@@ -977,7 +1084,8 @@ extern "C" int pcal_batch_step_graph(pcal_batch* b, const void* const* samples, 
         if (e == cudaSuccess) {
             const pcal_stats keep = b->stats;
             cudaError_t el = launch_call(b, d, gr.d_desc, gr.d_ctr, sh, cap);
-            if (el == cudaSuccess) el = launch_batch_finalize(b->d_ch, b->n, b->max_n, nullptr, cap);
+            int fl = 0;
+            if (el == cudaSuccess) el = batch_finalize_all(b, cap, &fl);
             b->stats = keep;
             e = cudaStreamEndCapture(cap, &graph);
             if (el != cudaSuccess) e = el;

@@ -491,7 +491,7 @@ extern "C" int pcal_dft_destroy(pcal_dft* d) {
     return PCAL_OK;
 }
 
-cudaError_t launch_dft(pcal_dft* d, const float2* P, int64_t C, float2* T, cudaStream_t s) {
+cudaError_t launch_dft(pcal_dft* d, const float2* P, int64_t C, float2* T, cudaStream_t s, unsigned int* err) {
     if (C <= 0) return cudaSuccess;
     if (d->mode == PCAL_DFT_FP32) {
         dft_fp32_kernel<<<(unsigned)C, 256, 2 * d->N * sizeof(float2), s>>>(P, T, d->N, d->d_tw);
@@ -505,7 +505,7 @@ cudaError_t launch_dft(pcal_dft* d, const float2* P, int64_t C, float2* T, cudaS
     a.n_cols = d->n_cols;
     a.k_chunks = d->k_chunks;
     a.w = d->d_w;
-    a.err = d->d_err;
+    a.err = err ? err : d->d_err;
     const dim3 grid((unsigned)((C + kTcM - 1) / kTcM), (unsigned)d->col_tiles);
     if (d->mode == PCAL_DFT_TC_TF32X3)
         dft_tc_kernel<PCAL_DFT_TC_TF32X3><<<grid, kTcThreads, kSmemTiles, s>>>(a);

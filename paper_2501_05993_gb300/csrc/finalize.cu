@@ -66,6 +66,7 @@ struct FinArgs {
     float2* T;     // FP32 tone phasors
     double* res;
     double* extra;  // post-processing, N+2 doubles (or null): peak delay, peak position, corrected bandpass phase
+    float2* Pout;   // cluster finalize: if set, store P here and stop before the DFT
     double fs_hz;
     unsigned int* ticket;
 };
@@ -848,6 +849,12 @@ __device__ __forceinline__ bool cluster_finalize(const FinArgs& a) {
         }
     }
     cluster.sync();  // P is complete in CTA 0; the other CTAs' Pr is no longer read
+    if (a.Pout) {
+        // the DFT runs elsewhere (the batched tensor-core DFT)
+        if (r == 0)
+            for (int i = t; i < N; i += blockDim.x) a.Pout[i] = sP[i];
+        return false;
+    }
     if (!big) {
         if (r != 0) return false;
         dft_range(sP, sTw, N, 0, N, sT);
@@ -878,13 +885,8 @@ __global__ void __launch_bounds__(kClusterThreads) fin_cluster_kernel(FinArgs a)
     cluster_finalize(a);
 }
 
-// Batch finalize: cluster c finalizes channel c of the batch from the
-// channel's device state, then starts the channel's next period.
-__global__ void __launch_bounds__(kClusterThreads) batch_fin_kernel(BatchChan* ch, const int* list) {
-    namespace cg = cooperative_groups;
-    const int i = (int)(blockIdx.x / cg::this_cluster().num_blocks());
-    const int c = list ? list[i] : i;
-    BatchChan& bc = ch[c];
+// Finalize arguments of one batched channel from its device state.
+__device__ inline FinArgs batch_fin_args(const BatchChan& bc) {
     const int64_t n_tot = bc.n_abs - bc.period_start;
     FinArgs a{};
     a.fmt = bc.fmt;
@@ -911,9 +913,44 @@ __global__ void __launch_bounds__(kClusterThreads) batch_fin_kernel(BatchChan* c
     a.res = bc.res;
     a.extra = bc.res + 5 * bc.N + 3;
     a.fs_hz = bc.fs;
+    return a;
+}
+
+// Batch finalize: cluster c finalizes channel c of the batch from the
+// channel's device state, then starts the channel's next period.  split:
+// stop after P (stored in the channel's P slot) for the batched DFT; the
+// products kernel finishes the channel.
+__global__ void __launch_bounds__(kClusterThreads) batch_fin_kernel(BatchChan* ch, const int* list, int split) {
+    namespace cg = cooperative_groups;
+    const int i = (int)(blockIdx.x / cg::this_cluster().num_blocks());
+    const int c = list ? list[i] : i;
+    BatchChan& bc = ch[c];
+    FinArgs a = batch_fin_args(bc);
+    if (split) a.Pout = bc.Pslot;
     // every CTA has read the state above before the first cluster barrier
     // inside, and rank 0 returns after the last one
     if (cluster_finalize(a) && threadIdx.x == 0) bc.period_start = bc.n_abs;
+}
+
+// After the batched DFT: block c runs channel c's products and
+// post-processing from its tone and P slots and starts its next period.
+__global__ void __launch_bounds__(kClusterThreads) batch_products_kernel(BatchChan* ch) {
+    BatchChan& bc = ch[blockIdx.x];
+    const FinArgs a = batch_fin_args(bc);
+    extern __shared__ __align__(16) uint8_t dsm[];
+    const ClusterSmem sm = cluster_layout(dsm, bc.N);
+    const int t = threadIdx.x;
+    for (int i = t; i < bc.N; i += blockDim.x) {
+        sm.sT[i] = bc.Tslot[i];
+        sm.sP[i] = bc.Pslot[i];
+    }
+    __syncthreads();
+    if (t < 32) tone_products_warp(a, sm.sT, sm.pm.psi, sm.pm.w, sm.pm.un, sm.pm.out);
+    else if (t < 64 && a.extra) peak_delay_warp(a, sm.sP);
+    __syncthreads();
+    write_results_block(a, sm.sT, sm.pm);
+    __syncthreads();
+    if (t == 0) bc.period_start = bc.n_abs;
 }
 
 // Spread DFT for large N; the last CTA runs the products.
@@ -1167,13 +1204,22 @@ cudaError_t prepare_batch_finalize() {
                                          (int)cluster_smem_bytes(kClusterBigN));
     if (e == cudaSuccess && C > 8)
         e = cudaFuncSetAttribute(batch_fin_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(batch_products_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)cluster_smem_bytes(kClusterBigN));
     return e;
+}
+
+cudaError_t launch_batch_products(BatchChan* d_ch, int n_ch, int max_n, cudaStream_t s) {
+    if (max_n > kClusterBigN) return cudaErrorInvalidValue;
+    batch_products_kernel<<<n_ch, kClusterThreads, cluster_smem_bytes(max_n), s>>>(d_ch);
+    return cudaGetLastError();
 }
 
 // prepare_batch_finalize() must have succeeded on this device (it makes the
 // CUDA calls that a stream capture does not allow).  max_n: the largest N of
 // the batch's channels.
-cudaError_t launch_batch_finalize(BatchChan* d_ch, int n_ch, int max_n, const int* d_list, cudaStream_t s) {
+cudaError_t launch_batch_finalize(BatchChan* d_ch, int n_ch, int max_n, const int* d_list, cudaStream_t s, int split) {
     const int C = cluster_size_for_device();
     if (C == 0) return cudaErrorNotSupported;
     if (max_n > kClusterBigN) return cudaErrorInvalidValue;
@@ -1189,7 +1235,7 @@ cudaError_t launch_batch_finalize(BatchChan* d_ch, int n_ch, int max_n, const in
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, batch_fin_kernel, d_ch, d_list);
+    return cudaLaunchKernelEx(&cfg, batch_fin_kernel, d_ch, d_list, split);
 }
 
 namespace {

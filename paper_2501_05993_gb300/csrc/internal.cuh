@@ -166,6 +166,8 @@ struct BatchChan {
     double fs;
     long long n_abs;            // samples accumulated since creation
     long long period_start;     // absolute index of the current period's first sample
+    float2* Pslot;              // batched-DFT finalize: this channel's row of P [N]
+    float2* Tslot;              // ... and of the tones [N]
 };
 
 // One (region, column group) of one call's bulk rows.
@@ -194,7 +196,16 @@ cudaError_t prepare_batch_finalize();
 cudaError_t launch_rot_finalize(const float4* acc, int lanes, int N, double fs, double fc, int64_t M,
                                 const float2* twN, double* res, cudaStream_t s);
 // Finalize channels list[i] (or i when list is null), i < n, with one cluster each.
-cudaError_t launch_batch_finalize(BatchChan* d_ch, int n, int max_n, const int* d_list, cudaStream_t s);
+// split: stop every channel after P (its P slot) for the batched DFT, which
+// launch_batch_products then finishes.
+cudaError_t launch_batch_finalize(BatchChan* d_ch, int n, int max_n, const int* d_list, cudaStream_t s,
+                                  int split = 0);
+cudaError_t launch_batch_products(BatchChan* d_ch, int n_ch, int max_n, cudaStream_t s);
+struct pcal_dft;
+// The batched tone DFT of dft_tc.cu (err: device error word, or null for the
+// DFT object's own).
+cudaError_t launch_dft(pcal_dft* d, const float2* P, int64_t C, float2* T, cudaStream_t s,
+                       unsigned int* err = nullptr);
 
 // ---- host side of the batched fold (shared by pcal_batch_* and the server) ----
 

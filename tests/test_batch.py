@@ -122,6 +122,41 @@ def test_batch_bins_and_phasors(pcal):
             check_results(b, c, ch, h)
 
 
+@pytest.mark.parametrize("mode", ["tf32x3", "bf16x3"])
+def test_batch_tensor_core_dft(pcal, mode):
+    """The finalize with the tone DFT as one tensor-core contraction per N: every channel's phasors and
+    post-processing within the stated tolerance of the oracle; the delay within 1e-2 sigma_td (the split
+    contraction keeps ~1e-6 of the phasors: on the strongest combs here, sigma_td ~ 7e-13 s, that moves
+    the delay by ~1e-3 sigma, where the CUDA-core FP32 DFT stays below 1e-3)."""
+    hosts = make_inputs(CHANNELS, seed=9)
+    keep, ptrs = upload(CHANNELS, hosts)
+    with pcal.Batch([c[:4] for c in CHANNELS]) as b:
+        b.set_dft(mode)
+        b.accumulate(ptrs, [c[4] for c in CHANNELS])
+        b.finalize_device()
+        assert b.stats()["kernel_launches"] >= 3  # clusters up to P, one DFT per N, products
+        for c, (ch, h) in enumerate(zip(CHANNELS, hosts)):
+            res = check_results(b, c, ch, h)
+            if ch[4]:
+                pr = oracle.products(oracle.tones_from_bins(oracle.bins(h, ch[3], 0, int(b.geometry[c].L)),
+                                                            *ch[:3]), ch[4], *ch[:3])
+                assert abs(res["td"] - pr["td"]) <= 1e-2 * pr["sigma_td"], (c, abs(res["td"] - pr["td"]) / pr["sigma_td"])
+        # a second period in the same mode, then back to the CUDA-core DFT
+        hosts2 = make_inputs(CHANNELS, seed=10, n0=[c[4] for c in CHANNELS])
+        keep2, ptrs2 = upload(CHANNELS, hosts2)
+        b.accumulate(ptrs2, [c[4] for c in CHANNELS])
+        b.finalize_device()
+        for c, (ch, h) in enumerate(zip(CHANNELS, hosts2)):
+            check_results(b, c, ch, h, n0=ch[4])
+        b.set_dft("fp32")
+        hosts3 = make_inputs(CHANNELS, seed=11, n0=[2 * c[4] for c in CHANNELS])
+        keep3, ptrs3 = upload(CHANNELS, hosts3)
+        b.accumulate(ptrs3, [c[4] for c in CHANNELS])
+        b.finalize_device()
+        for c, (ch, h) in enumerate(zip(CHANNELS, hosts3)):
+            check_results(b, c, ch, h, n0=2 * ch[4])
+
+
 @pytest.mark.parametrize("sched", [
     dict(ctas=152, box_rows=32, static_pct=0, min_chunk=1, col_cap=224),
     dict(ctas=37, box_rows=64, static_pct=100, min_chunk=8, col_cap=128),
@@ -185,13 +220,15 @@ def test_batch_two_calls_and_two_periods(pcal):
             check_results(b, c, ch, h, n0=ch[4])
 
 
-def test_batch_graph_replay(pcal):
+@pytest.mark.parametrize("mode", ["fp32", "tf32x3"])
+def test_batch_graph_replay(pcal, mode):
     """A captured step replayed on refilled buffers gives each period's
-    oracle results."""
+    oracle results (with either DFT of the finalize)."""
     import torch
 
     chans = CHANNELS[:6]
     with pcal.Batch([c[:4] for c in chans]) as b:
+        b.set_dft(mode)
         hosts = make_inputs(chans, seed=40)
         keep, ptrs = upload(chans, hosts)
         n = [ch[4] for ch in chans]
