@@ -89,6 +89,15 @@ def read_peaks():
         return 6800.0, "fallback"
 
 
+def read_tensor_peak():
+    """Measured dense bf16 tensor throughput (burst, TFLOP/s), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
 def read_batch_traffic_ratio():
     """DRAM bytes per sample byte of the batched fold from its committed ncu
     summary (captured on a reduced batch), or None when batch.cu changed."""
@@ -416,6 +425,9 @@ def run_gpu(args):
             torch.cuda.empty_cache()
             out["serving"] = summarize_extra(lambda: run_serve(extra_args(args), emit=False),
                                              ("p50_ms", "p99_ms", "periods", "realtime", "saturation", "config"))
+            torch.cuda.empty_cache()
+            out["tensor_dft"] = summarize_extra(lambda: run_tensor_dft(extra_args(args), emit=False),
+                                                ("modes", "speedup_vs_fp32", "config"))
         print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
@@ -635,6 +647,21 @@ def run_batch(args, emit=True):
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"direct FP64 definition over the first {args.cpu_sample} samples of a 2-bit channel "
                          f"({dt:.1f} s)"}
+    # the finalize alone with each tone DFT (fused CUDA-core FP32 vs one tensor-core contraction per N)
+    fin_modes = {}
+    for mode in ("fp32", "tf32x3", "bf16x3"):
+        batch.set_dft(mode)
+        batch.accumulate(ptrs, n, stream)
+        for _ in range(3):
+            batch.finalize_device(stream)
+        k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k0.record(stream)
+        for _ in range(20):
+            batch.finalize_device(stream)
+        k1.record(stream)
+        torch.cuda.synchronize()
+        fin_modes[mode] = k0.elapsed_time(k1) / 20
+    batch.set_dft("fp32")
     batch.close()
     value = world * total_samples / (batched_ms / 1e3) / 1e9
     if rank == 0:
@@ -648,7 +675,8 @@ def run_batch(args, emit=True):
                        "max_L": max(int(g.L) for g in batch.geometry), "schedule": chosen,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": f"{total_bytes >> 30} GB of inputs per step > L2",
-                       "fold_ms": fold_ms, "batched_vs_plain_max_phasor_diff": worst},
+                       "fold_ms": fold_ms, "batched_vs_plain_max_phasor_diff": worst,
+                       "finalize_ms_by_dft": fin_modes},
             "plain": {"value": world * total_samples / (plain_ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": plain_ms,
                       "steps": k_plain, "launches": "per channel: fold + ragged + finalize"},
             "graph": {"value": world * total_samples / (graph_ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": graph_ms},
@@ -658,6 +686,65 @@ def run_batch(args, emit=True):
             print(json.dumps(out))
         return out
     return None
+
+
+# ---- batched tone DFT on the tensor cores ------------------------------------------------
+
+DFT_WORKLOAD = "batched tone DFT, 4096 channels x N 1024 (complex64 P -> T), seeded complex Gaussian P plus a pulse"
+
+
+def run_tensor_dft(args, emit=True, C=4096, N=1024, reps=20):
+    """pcal_dft_execute in every mode on one batch of P: time per launch (CUDA events over back-to-back
+    launches), achieved TFLOP/s of the algorithmic contraction against the measured tensor peak, and the
+    error against the DFT definition in FP64."""
+    import torch
+
+    import paper_2501_05993_gb300 as pcal
+    from paper_2501_05993_gb300 import build as libbuild
+
+    libbuild.build()
+    pcal.load()
+    rng = np.random.default_rng(2501059932 + 5)
+    P = (rng.standard_normal((C, N)) + 1j * rng.standard_normal((C, N))).astype(np.complex64)
+    P += (3 * np.sqrt(N) * np.exp(2j * np.pi * rng.integers(0, N, (C, 1)) * np.arange(N) / N)).astype(np.complex64)
+    ref = np.fft.fft(P.astype(np.complex128), axis=1)
+    dP = torch.from_numpy(P).cuda()
+    dT = torch.empty((C, N), dtype=torch.complex64, device="cuda")
+    peak_bf16, peak_kind = read_tensor_peak()
+    modes = {}
+    for mode in ("fp32", "tf32x3", "bf16x3"):
+        with pcal.Dft(N, mode) as d:
+            for _ in range(3):
+                d.execute(dP, C, dT)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                d.execute(dP, C, dT)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            flags = d.check()
+        T = dT.cpu().numpy()
+        err = np.max(np.abs(T - ref), axis=1) / np.max(np.abs(ref), axis=1)
+        if mode == "fp32":
+            flops = 8.0 * C * N * N  # complex MACs on CUDA cores
+            roof = None
+        else:
+            flops = 3 * 2.0 * C * (2 * N) * (2 * N)  # three real C x 2N x 2N products
+            # TF32 from the measured bf16 peak and the nominal dense ratio (1.1 / 2.25 PFLOP/s)
+            peak = peak_bf16 * (1.1 / 2.25) if mode == "tf32x3" else peak_bf16
+            ach = flops / (ms / 1e3) / 1e12
+            roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                    "traffic": None, "peak_kind": f"{peak_kind} bf16 burst" + (" x 1.1/2.25 (tf32)" if mode == "tf32x3" else "")}
+        modes[mode] = {"ms": ms, "tflops": flops / (ms / 1e3) / 1e12, "max_rel_err": float(err.max()),
+                       "median_rel_err": float(np.median(err)), "device_error_bits": flags, "roofline": roof}
+    out = {"metric": "batched tone DFT time per launch", "value": modes["bf16x3"]["ms"], "unit": "ms",
+           "higher_is_better": False, "data": "synthetic", "config": {"workload": DFT_WORKLOAD, "C": C, "N": N},
+           "modes": modes,
+           "speedup_vs_fp32": {m: modes["fp32"]["ms"] / modes[m]["ms"] for m in ("tf32x3", "bf16x3")}}
+    if emit:
+        print(json.dumps(out))
+    return out
 
 
 # ---- serving workload: 256 live streams, 10 ms chunks, Poisson arrivals ------------------
@@ -894,7 +981,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="single workload: skip the batched and serving summaries")
     ap.add_argument("--prec-scale", type=float, default=1.0, help="precision workload: fraction of the 16 s")
     ap.add_argument("--prec-lanes", type=int, default=128)
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "precision"],
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "precision", "dft"],
                     help="single: the 2-bit single-channel headline workload; batch: 64 mixed channels")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -907,6 +994,8 @@ def main():
         run_serve(args)
     elif args.workload == "precision":
         run_precision(args)
+    elif args.workload == "dft":
+        run_tensor_dft(args)
     else:
         run_gpu(args)
 
