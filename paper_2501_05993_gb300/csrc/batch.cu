@@ -901,7 +901,9 @@ extern "C" int pcal_batch_set_dft(pcal_batch* b, int mode) {
         for (DftGroup& g : b->dft) {
             if (rc != PCAL_OK) break;
             const size_t bytes = (size_t)g.count * g.N * sizeof(float2);
-            if (cudaMalloc(&g.dP, bytes) != cudaSuccess || cudaMalloc(&g.dT, bytes) != cudaSuccess) rc = PCAL_ENOMEM;
+            if (cudaMalloc(&g.dP, bytes) != cudaSuccess || cudaMalloc(&g.dT, bytes) != cudaSuccess ||
+                dft_reserve(g.dft, g.count) != cudaSuccess)
+                rc = PCAL_ENOMEM;
             int row = 0;
             for (BatchChan& c : b->h_ch)
                 if (rc == PCAL_OK && c.N == g.N) {

@@ -42,7 +42,6 @@ constexpr int kTcThreads = 256;        // 8 warps
 constexpr int kChunkBytes = 128;       // bytes of K per row and chunk
 constexpr int kATile = kTcM * kChunkBytes;      // 16 KB
 constexpr int kBTile = kTcNMax * kChunkBytes;   // 16 KB
-constexpr int kSmemTiles = 2 * kATile + 2 * kBTile;  // hi and lo of A and B: 64 KB
 constexpr int kTmemCols = 512;                  // three accumulators of kTcNMax columns (a power of two)
 
 // Byte offset of element (r, k) of a rows x (128 bytes of K) tile, elements
@@ -195,31 +194,66 @@ __device__ __forceinline__ uint32_t instr_desc(int n) {
 }
 
 struct DftTcArgs {
-    const float2* P;   // [C][N]
     float2* T;         // [C][N]
     int64_t C;
     int N;
     int n_cols;        // 2N rounded up to 16
     int k_chunks;      // chunks of K = 2N
+    const uint8_t* a;  // operand tiles of P: [row tile][chunk] x (hi, lo) x kATile bytes
     const uint8_t* w;  // weight tiles: [column tile][chunk] x (hi, lo) x kBTile bytes
     unsigned int* err;
 };
 
+// P -> split operand tiles: row tile mt, chunk kc holds rows 128 mt.. and K
+// values kc*KC.. of [Re P | Im P] (zeros past C and 2N) as hi and lo tile
+// images.  One thread per (row, K value).
+template <int MODE>
+__global__ void split_p_kernel(const float2* __restrict__ P, int64_t C, int N, int k_chunks, uint8_t* __restrict__ out,
+                               int64_t total) {
+    constexpr int ES = esize_of<MODE>();
+    constexpr int KC = kChunkBytes / ES;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        // e = ((mt * k_chunks + kc) * 128 + r) * KC + k
+        const int k = (int)(e % KC);
+        const int64_t rest = e / KC;
+        const int r = (int)(rest % kTcM);
+        const int64_t blk = rest / kTcM;
+        const int kc = (int)(blk % k_chunks);
+        const int64_t mt = blk / k_chunks;
+        const int64_t c = mt * kTcM + r;
+        const int kk = kc * KC + k;
+        float x = 0.f;
+        if (c < C && kk < 2 * N) {
+            const float2 v = P[c * N + (kk < N ? kk : kk - N)];
+            x = kk < N ? v.x : v.y;
+        }
+        uint8_t* base = out + (size_t)blk * 2 * kATile;
+        const uint32_t o = tile_offset(r, k, kTcM, ES);
+        split_store<MODE>(x, base + o, base + kATile + o);
+    }
+}
+
+constexpr int kStages = 3;
+constexpr int kStageBytes = 2 * kATile + 2 * kBTile;  // A hi, A lo, B hi, B lo: 64 KB
+constexpr int kSmemTiles = kStages * kStageBytes;      // 192 KB: one CTA (and its 512 TMEM columns) per SM
+
+// One CTA: 128 channels x up to 128 output columns.  Thread 0 streams the A
+// and B tile pairs of each chunk through kStages shared-memory stages (bulk
+// copies, full barriers); thread 32 issues the chunk's 4 K-steps x 3 products
+// and commits them to the stage's empty barrier, so a stage is refilled as
+// soon as the MMAs that read it are done; a last commit signals the epilogue.
 template <int MODE>
 __global__ void __launch_bounds__(kTcThreads, 1) dft_tc_kernel(const DftTcArgs a) {
     constexpr int ES = esize_of<MODE>();
     constexpr int KC = kChunkBytes / ES;  // K values per chunk
     constexpr int KS = 32 / ES;           // K values per MMA
     extern __shared__ __align__(1024) uint8_t smem[];
-    uint8_t* a_hi = smem;
-    uint8_t* a_lo = smem + kATile;
-    uint8_t* b_hi = smem + 2 * kATile;
-    uint8_t* b_lo = smem + 2 * kATile + kBTile;
-    __shared__ __align__(8) uint64_t bar_w, bar_mma;
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
     __shared__ uint32_t s_tmem;
     __shared__ int s_fail;
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int64_t m0 = (int64_t)blockIdx.x * kTcM;
+    const int64_t mt = blockIdx.x;
+    const int64_t m0 = mt * kTcM;
     const int n0 = blockIdx.y * kTcNMax;
     const int nt = a.n_cols - n0 < kTcNMax ? a.n_cols - n0 : kTcNMax;  // a multiple of 16
     const uint32_t w_bytes = (uint32_t)nt * kChunkBytes;
@@ -228,8 +262,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) dft_tc_kernel(const DftTcArgs a
         tc_relinquish();
     }
     if (tid == 32) {
-        mbar_init(&bar_w, 1);
-        mbar_init(&bar_mma, 1);
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&done, 1);
         s_fail = 0;
         fence_barrier_init();
     }
@@ -237,68 +274,67 @@ __global__ void __launch_bounds__(kTcThreads, 1) dft_tc_kernel(const DftTcArgs a
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s_tmem;
-    const uint32_t idesc = instr_desc<MODE>(nt);
-    const uint8_t* wtile = a.w + (size_t)blockIdx.y * a.k_chunks * 2 * kBTile;
-    int issued = 0;  // chunks whose MMAs were committed
-    for (int kc = 0; kc < a.k_chunks; ++kc) {
-        if (tid == 0) {
-            mbar_arrive_expect_tx(&bar_w, 2 * w_bytes);
-            bulk_load(b_hi, wtile + (size_t)kc * 2 * kBTile, w_bytes, &bar_w);
-            bulk_load(b_lo, wtile + (size_t)kc * 2 * kBTile + kBTile, w_bytes, &bar_w);
-        }
-        // A: rows m0.., K values kc*KC.. of [Re P | Im P], split in two
-        for (int e = tid; e < kTcM * KC; e += kTcThreads) {
-            const int r = e / KC, k = e % KC;
-            const int64_t c = m0 + r;
-            const int kk = kc * KC + k;
-            float x = 0.f;
-            if (c < a.C && kk < 2 * a.N) {
-                const float2 p = a.P[c * a.N + (kk < a.N ? kk : kk - a.N)];
-                x = kk < a.N ? p.x : p.y;
+    if (tid == 0) {
+        // ---- producer ----
+        const uint8_t* atile = a.a + (size_t)mt * a.k_chunks * 2 * kATile;
+        const uint8_t* wtile = a.w + (size_t)blockIdx.y * a.k_chunks * 2 * kBTile;
+        int issued = 0;
+        for (int kc = 0; kc < a.k_chunks; ++kc) {
+            const int s = kc % kStages;
+            if (kc >= kStages && !mbar_wait(&empty[s], (uint32_t)((kc / kStages - 1) & 1))) {
+                atomicOr(a.err, PCAL_DERR_EMPTY_WAIT);
+                s_fail = 1;
+                break;
             }
-            const uint32_t o = tile_offset(r, k, kTcM, ES);
-            split_store<MODE>(x, a_hi + o, a_lo + o);
+            issued = kc + 1;
+            uint8_t* st = smem + (size_t)s * kStageBytes;
+            mbar_arrive_expect_tx(&full[s], 2 * kATile + 2 * w_bytes);
+            bulk_load(st, atile + (size_t)kc * 2 * kATile, 2 * kATile, &full[s]);
+            bulk_load(st + 2 * kATile, wtile + (size_t)kc * 2 * kBTile, w_bytes, &full[s]);
+            bulk_load(st + 2 * kATile + kBTile, wtile + (size_t)kc * 2 * kBTile + kBTile, w_bytes, &full[s]);
         }
-        fence_proxy_async_smem();
-        __syncthreads();
-        if (tid == 0) {
-            if (!mbar_wait(&bar_w, (uint32_t)(kc & 1))) {
+        if (s_fail) {
+            // copies in flight must land before the CTA's shared memory is reused
+            for (int kc = issued - kStages > 0 ? issued - kStages : 0; kc < issued; ++kc)
+                if (!mbar_wait(&full[kc % kStages], (uint32_t)((kc / kStages) & 1))) atomicOr(a.err, PCAL_DERR_DRAIN_WAIT);
+        }
+    } else if (tid == 32) {
+        // ---- MMA issuer ----
+        const uint32_t idesc = instr_desc<MODE>(nt);
+        const uint32_t lbo_a = (kTcM / 8) * 128, lbo_b = (uint32_t)(nt / 8) * 128;
+        bool ok = true;
+        for (int kc = 0; kc < a.k_chunks; ++kc) {
+            const int s = kc % kStages;
+            if (!mbar_wait(&full[s], (uint32_t)((kc / kStages) & 1))) {
                 atomicOr(a.err, PCAL_DERR_FULL_WAIT);
                 s_fail = 1;
-                // the copies must land before the CTA's shared memory is reused
-                if (!mbar_wait(&bar_w, (uint32_t)(kc & 1))) atomicOr(a.err, PCAL_DERR_DRAIN_WAIT);
-            } else {
-                tc_fence_after();
-                const uint32_t lbo_a = (kTcM / 8) * 128, lbo_b = (uint32_t)(nt / 8) * 128;
-                for (int s = 0; s < KC / KS; ++s) {
-                    // K-step s: two core matrices along K
-                    const uint32_t oa = (uint32_t)s * 2 * lbo_a, ob = (uint32_t)s * 2 * lbo_b;
-                    const uint64_t ah = smem_desc(smem_addr(a_hi) + oa, lbo_a, 128);
-                    const uint64_t al = smem_desc(smem_addr(a_lo) + oa, lbo_a, 128);
-                    const uint64_t bh = smem_desc(smem_addr(b_hi) + ob, lbo_b, 128);
-                    const uint64_t bl = smem_desc(smem_addr(b_lo) + ob, lbo_b, 128);
-                    // hi.hi: even / odd chunks; cross products: one accumulator
-                    const uint32_t d_hh = tmem + (uint32_t)(kc & 1) * kTcNMax, d_x = tmem + 2 * kTcNMax;
-                    tc_mma<MODE>(d_hh, ah, bh, idesc, (kc < 2 && s == 0) ? 0u : 1u);
-                    tc_mma<MODE>(d_x, ah, bl, idesc, (kc == 0 && s == 0) ? 0u : 1u);
-                    tc_mma<MODE>(d_x, al, bh, idesc, 1u);
-                }
-                tc_commit(&bar_mma);
+                ok = false;
+                break;
             }
+            tc_fence_after();
+            const uint32_t st = smem_addr(smem + (size_t)s * kStageBytes);
+            const uint32_t a_hi = st, a_lo = st + kATile, b_hi = st + 2 * kATile, b_lo = st + 2 * kATile + kBTile;
+            // hi.hi: even / odd chunks; cross products: one accumulator
+            const uint32_t d_hh = tmem + (uint32_t)(kc & 1) * kTcNMax, d_x = tmem + 2 * kTcNMax;
+#pragma unroll
+            for (int k = 0; k < KC / KS; ++k) {
+                const uint32_t oa = (uint32_t)k * 2 * lbo_a, ob = (uint32_t)k * 2 * lbo_b;
+                const uint64_t ah = smem_desc(a_hi + oa, lbo_a, 128), al = smem_desc(a_lo + oa, lbo_a, 128);
+                const uint64_t bh = smem_desc(b_hi + ob, lbo_b, 128), bl = smem_desc(b_lo + ob, lbo_b, 128);
+                tc_mma<MODE>(d_hh, ah, bh, idesc, (kc < 2 && k == 0) ? 0u : 1u);
+                tc_mma<MODE>(d_x, ah, bl, idesc, (kc == 0 && k == 0) ? 0u : 1u);
+                tc_mma<MODE>(d_x, al, bh, idesc, 1u);
+            }
+            tc_commit(&empty[s]);  // the stage is free once these MMAs are done
         }
-        __syncthreads();
-        if (s_fail) break;
-        issued = kc + 1;
-        // the MMAs read the tiles: wait before the next chunk overwrites them
-        if (!mbar_wait(&bar_mma, (uint32_t)(kc & 1))) {
-            atomicOr(a.err, PCAL_DERR_FULL_WAIT);
-            s_fail = 1;
-        }
-        __syncthreads();
-        if (s_fail) break;
+        if (ok) tc_commit(&done);
     }
+    // every thread: wait for the last MMAs (the issuer committed `done`)
+    __syncthreads();
+    const bool have = !s_fail && mbar_wait(&done, 0);
+    if (!have && tid == 0) atomicOr(a.err, PCAL_DERR_DRAIN_WAIT);
     tc_fence_after();
-    if (!s_fail && issued == a.k_chunks) {
+    if (have) {
         // epilogue: warp w reads TMEM lanes 32 (w % 4) .. (rows), column half
         // w / 4, and adds the three accumulators
         const int q = warp & 3, half = warp >> 2;
@@ -365,6 +401,8 @@ __global__ void dft_fp32_kernel(const float2* __restrict__ P, float2* __restrict
 struct pcal_dft {
     int N, mode, n_cols, k_chunks, col_tiles;
     uint8_t* d_w;     // weight tiles (tensor-core modes)
+    uint8_t* d_a;     // operand tiles of P (workspace)
+    size_t a_cap;     // bytes of d_a
     float2* d_tw;     // FP32 twiddles (CUDA-core mode)
     unsigned int* d_err;
 };
@@ -485,10 +523,24 @@ extern "C" int pcal_dft_destroy(pcal_dft* d) {
     if (!d) return PCAL_OK;
     cudaDeviceSynchronize();
     cudaFree(d->d_w);
+    cudaFree(d->d_a);
     cudaFree(d->d_tw);
     cudaFree(d->d_err);
     delete d;
     return PCAL_OK;
+}
+
+// Operand workspace for C channels (allocates: not under stream capture).
+cudaError_t dft_reserve(pcal_dft* d, int64_t C) {
+    if (d->mode == PCAL_DFT_FP32 || C <= 0) return cudaSuccess;
+    const size_t need = (size_t)((C + kTcM - 1) / kTcM) * d->k_chunks * 2 * kATile;
+    if (need <= d->a_cap) return cudaSuccess;
+    cudaFree(d->d_a);
+    d->d_a = nullptr;
+    d->a_cap = 0;
+    const cudaError_t e = cudaMalloc(&d->d_a, need);
+    if (e == cudaSuccess) d->a_cap = need;
+    return e;
 }
 
 cudaError_t launch_dft(pcal_dft* d, const float2* P, int64_t C, float2* T, cudaStream_t s, unsigned int* err) {
@@ -497,16 +549,24 @@ cudaError_t launch_dft(pcal_dft* d, const float2* P, int64_t C, float2* T, cudaS
         dft_fp32_kernel<<<(unsigned)C, 256, 2 * d->N * sizeof(float2), s>>>(P, T, d->N, d->d_tw);
         return cudaGetLastError();
     }
+    const int64_t m_tiles = (C + kTcM - 1) / kTcM;
+    if ((size_t)m_tiles * d->k_chunks * 2 * kATile > d->a_cap) return cudaErrorInvalidValue;  // dft_reserve first
+    const int64_t total = m_tiles * d->k_chunks * kTcM * (kChunkBytes / (d->mode == PCAL_DFT_TC_TF32X3 ? 4 : 2));
+    const int sgrid = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+    if (d->mode == PCAL_DFT_TC_TF32X3)
+        split_p_kernel<PCAL_DFT_TC_TF32X3><<<sgrid, 256, 0, s>>>(P, C, d->N, d->k_chunks, d->d_a, total);
+    else
+        split_p_kernel<PCAL_DFT_TC_BF16X3><<<sgrid, 256, 0, s>>>(P, C, d->N, d->k_chunks, d->d_a, total);
     DftTcArgs a{};
-    a.P = P;
     a.T = T;
+    a.a = d->d_a;
     a.C = C;
     a.N = d->N;
     a.n_cols = d->n_cols;
     a.k_chunks = d->k_chunks;
     a.w = d->d_w;
     a.err = err ? err : d->d_err;
-    const dim3 grid((unsigned)((C + kTcM - 1) / kTcM), (unsigned)d->col_tiles);
+    const dim3 grid((unsigned)m_tiles, (unsigned)d->col_tiles);
     if (d->mode == PCAL_DFT_TC_TF32X3)
         dft_tc_kernel<PCAL_DFT_TC_TF32X3><<<grid, kTcThreads, kSmemTiles, s>>>(a);
     else
@@ -517,6 +577,10 @@ cudaError_t launch_dft(pcal_dft* d, const float2* P, int64_t C, float2* T, cudaS
 extern "C" int pcal_dft_execute(pcal_dft* d, const void* P, int64_t C, void* T, void* stream) {
     if (!d || C < 0 || (C > 0 && (!P || !T))) return PCAL_EINVAL;
     if (C > (int64_t)65535 * kTcM) return PCAL_ETOOLARGE;
+    if (dft_reserve(d, C) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return PCAL_ENOMEM;
+    }
     const cudaError_t e = launch_dft(d, static_cast<const float2*>(P), C, static_cast<float2*>(T),
                                      static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? PCAL_OK : PCAL_ECUDA;

@@ -206,6 +206,8 @@ struct pcal_dft;
 // DFT object's own).
 cudaError_t launch_dft(pcal_dft* d, const float2* P, int64_t C, float2* T, cudaStream_t s,
                        unsigned int* err = nullptr);
+// Operand workspace of launch_dft for up to C channels (allocates).
+cudaError_t dft_reserve(pcal_dft* d, int64_t C);
 
 // ---- host side of the batched fold (shared by pcal_batch_* and the server) ----
 
