@@ -139,6 +139,16 @@ int pcal_accumulate(pcal_plan* plan, const void* samples, int64_t n, void* strea
 int pcal_accumulate_host(pcal_plan* plan, const void* host_samples, int64_t n, void* stream);
 
 /*
+ * pcal_accumulate_host_async -- as pcal_accumulate_host, but returns as soon
+ * as the copies and folds are queued: the host buffer must stay unchanged
+ * until `stream` has passed this call's folds (a later synchronising call on
+ * the plan, a stream synchronisation, or pcal_read_async_results of a period
+ * finalized after it).  Lets a host loop queue the next period's copies
+ * while the link is still busy with this one.
+ */
+int pcal_accumulate_host_async(pcal_plan* plan, const void* host_samples, int64_t n, void* stream);
+
+/*
  * pcal_finalize_device -- end the current integration period on `stream`
  * (NULL = the stream of the last accumulate):  decode the bins, rotate each
  * of the L bins by exp(-j*2*pi*f_offset*k/fs) in FP64 (Eq. 3), fold them to
@@ -167,6 +177,20 @@ int pcal_finalize(pcal_plan* plan, double* phasors_out);
  */
 int pcal_read_results(pcal_plan* plan, double* phasors, double* amp, double* phase, double* unwrapped,
                       double* td_s, double* sigma_td_s);
+
+/*
+ * Pipelined results.  pcal_finalize_async -- pcal_finalize_device on
+ * `stream`, then an asynchronous copy of the period's results (the 5N+3
+ * values of pcal_read_results and the device error bits) into a pinned ring
+ * of two slots; returns at once.  pcal_read_async_results -- wait for the
+ * results of the period finalized `age` pcal_finalize_async calls ago (0 =
+ * the latest, 1 = the one before; a slot is reused two calls later) and
+ * copy them out as pcal_read_results does.  PCAL_EINVAL for an age not held
+ * in the ring, PCAL_ETIMEOUT if a bounded device wait of that period gave up.
+ */
+int pcal_finalize_async(pcal_plan* plan, void* stream);
+int pcal_read_async_results(pcal_plan* plan, int age, double* phasors, double* amp, double* phase,
+                            double* unwrapped, double* td_s, double* sigma_td_s);
 
 /* pcal_get_delay -- delay and its 1-sigma of the last finalize (host). */
 int pcal_get_delay(pcal_plan* plan, double* td_s, double* sigma_td_s);

@@ -120,6 +120,9 @@ def load(path: str | None = None):
         "pcal_plan_set_levels": ([vp, P(dbl)], ci),
         "pcal_accumulate": ([vp, vp, i64, vp], ci),
         "pcal_accumulate_host": ([vp, vp, i64, vp], ci),
+        "pcal_accumulate_host_async": ([vp, vp, i64, vp], ci),
+        "pcal_finalize_async": ([vp, vp], ci),
+        "pcal_read_async_results": ([vp, ci, vp, vp, vp, vp, vp, vp], ci),
         "pcal_finalize_device": ([vp, vp], ci),
         "pcal_finalize": ([vp, vp], ci),
         "pcal_read_results": ([vp, vp, vp, vp, vp, vp, vp], ci),
@@ -241,6 +244,30 @@ def pcal_accumulate_host(plan: int, host: np.ndarray, n: int, stream=None) -> No
     if not host.flags.c_contiguous:
         raise ValueError("host samples must be C-contiguous")
     _check(load().pcal_accumulate_host(plan, host.ctypes.data, int(n), _stream(stream)), "pcal_accumulate_host")
+
+
+def pcal_accumulate_host_async(plan: int, host: np.ndarray, n: int, stream=None) -> None:
+    """As pcal_accumulate_host without waiting for the copies: `host` must stay unchanged until the
+    stream has passed this call's folds."""
+    if not host.flags.c_contiguous:
+        raise ValueError("host samples must be C-contiguous")
+    _check(load().pcal_accumulate_host_async(plan, host.ctypes.data, int(n), _stream(stream)),
+           "pcal_accumulate_host_async")
+
+
+def pcal_finalize_async(plan: int, stream=None) -> None:
+    _check(load().pcal_finalize_async(plan, _stream(stream)), "pcal_finalize_async")
+
+
+def pcal_read_async_results(plan: int, n_tones: int, age: int = 0) -> dict:
+    ph = np.zeros(2 * n_tones)
+    amp, phase, un = np.zeros(n_tones), np.zeros(n_tones), np.zeros(n_tones)
+    td, sg = ctypes.c_double(), ctypes.c_double()
+    _check(load().pcal_read_async_results(plan, int(age), ph.ctypes.data, amp.ctypes.data, phase.ctypes.data,
+                                          un.ctypes.data, ctypes.addressof(td), ctypes.addressof(sg)),
+           "pcal_read_async_results")
+    return {"phasors": ph[0::2] + 1j * ph[1::2], "amp": amp, "phase": phase, "unwrapped": un, "td": td.value,
+            "sigma_td": sg.value}
 
 
 def pcal_finalize_device(plan: int, stream=None) -> None:
@@ -369,8 +396,19 @@ class Plan:
             n = host.size * (4 if self.fmt == "2bit" else 1)
         pcal_accumulate_host(self.handle, host, n, stream)
 
+    def accumulate_host_async(self, host: np.ndarray, n: int | None = None, stream=None):
+        if n is None:
+            n = host.size * (4 if self.fmt == "2bit" else 1)
+        pcal_accumulate_host_async(self.handle, host, n, stream)
+
     def finalize_device(self, stream=None):
         pcal_finalize_device(self.handle, stream)
+
+    def finalize_async(self, stream=None):
+        pcal_finalize_async(self.handle, stream)
+
+    def read_async(self, age: int = 0) -> dict:
+        return pcal_read_async_results(self.handle, self.N, age)
 
     def finalize(self) -> np.ndarray:
         return pcal_finalize(self.handle, self.N)

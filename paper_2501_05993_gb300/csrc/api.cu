@@ -43,6 +43,10 @@ void free_plan(pcal_plan* p) {
     }
     if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
     if (p->h_res) cudaFreeHost(p->h_res);
+    for (int i = 0; i < 2; ++i) {
+        if (p->h_ring[i]) cudaFreeHost(p->h_ring[i]);
+        if (p->ring_ev[i]) cudaEventDestroy(p->ring_ev[i]);
+    }
     if (p->h_hint) cudaFreeHost(p->h_hint);
     delete p;
 }
@@ -208,7 +212,9 @@ extern "C" int pcal_accumulate(pcal_plan* p, const void* samples, int64_t n, voi
     return PCAL_OK;
 }
 
-extern "C" int pcal_accumulate_host(pcal_plan* p, const void* host, int64_t n, void* stream) {
+namespace {
+
+int accumulate_host_impl(pcal_plan* p, const void* host, int64_t n, void* stream, bool wait) {
     if (!p || n < 0) return PCAL_EINVAL;
     if (n == 0) return PCAL_OK;
     if (!host) return PCAL_EINVAL;
@@ -252,8 +258,18 @@ extern "C" int pcal_accumulate_host(pcal_plan* p, const void* host, int64_t n, v
         j ^= 1;
     }
     // the host buffer may be reused once its copies are done
-    e = cudaStreamSynchronize(p->copy_stream);
+    if (wait) e = cudaStreamSynchronize(p->copy_stream);
     return cuda_status(e);
+}
+
+}  // namespace
+
+extern "C" int pcal_accumulate_host(pcal_plan* p, const void* host, int64_t n, void* stream) {
+    return accumulate_host_impl(p, host, n, stream, true);
+}
+
+extern "C" int pcal_accumulate_host_async(pcal_plan* p, const void* host, int64_t n, void* stream) {
+    return accumulate_host_impl(p, host, n, stream, false);
 }
 
 extern "C" int pcal_finalize_device(pcal_plan* p, void* stream) {
@@ -289,6 +305,49 @@ extern "C" int pcal_read_results(pcal_plan* p, double* phasors, double* amp, dou
     if (unwrapped) memcpy(unwrapped, p->h_res + 4 * N, N * sizeof(double));
     if (td) *td = p->h_res[5 * N];
     if (sigma) *sigma = p->h_res[5 * N + 1];
+    return PCAL_OK;
+}
+
+extern "C" int pcal_finalize_async(pcal_plan* p, void* stream) {
+    if (!p) return PCAL_EINVAL;
+    const int64_t N = p->g.N;
+    const size_t bytes = (5 * N + 3) * sizeof(double);
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        if (!p->h_ring[i]) e = cudaMallocHost(reinterpret_cast<void**>(&p->h_ring[i]), bytes + sizeof(double));
+        if (e == cudaSuccess && !p->ring_ev[i]) e = cudaEventCreateWithFlags(&p->ring_ev[i], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+    const int rc = pcal_finalize_device(p, stream);
+    if (rc != PCAL_OK) return rc;
+    const int slot = (int)(p->ring_count % 2);
+    double* h = p->h_ring[slot];
+    e = cudaMemcpyAsync(h, p->d_res, bytes, cudaMemcpyDeviceToHost, p->last_stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h + 5 * N + 3, p->d_err, sizeof(unsigned int), cudaMemcpyDeviceToHost, p->last_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(p->ring_ev[slot], p->last_stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    ++p->ring_count;
+    return PCAL_OK;
+}
+
+extern "C" int pcal_read_async_results(pcal_plan* p, int age, double* phasors, double* amp, double* phase,
+                                       double* unwrapped, double* td, double* sigma) {
+    if (!p || age < 0 || age > 1 || age >= p->ring_count) return PCAL_EINVAL;
+    const int64_t N = p->g.N;
+    const int slot = (int)((p->ring_count - 1 - age) % 2);
+    const cudaError_t e = cudaEventSynchronize(p->ring_ev[slot]);
+    if (e != cudaSuccess) return cuda_status(e);
+    const double* h = p->h_ring[slot];
+    unsigned int err;
+    memcpy(&err, h + 5 * N + 3, sizeof(err));
+    if (err) return PCAL_ETIMEOUT;
+    if (phasors) memcpy(phasors, h, 2 * N * sizeof(double));
+    if (amp) memcpy(amp, h + 2 * N, N * sizeof(double));
+    if (phase) memcpy(phase, h + 3 * N, N * sizeof(double));
+    if (unwrapped) memcpy(unwrapped, h + 4 * N, N * sizeof(double));
+    if (td) *td = h[5 * N];
+    if (sigma) *sigma = h[5 * N + 1];
     return PCAL_OK;
 }
 

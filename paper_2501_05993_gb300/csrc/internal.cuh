@@ -106,6 +106,9 @@ struct pcal_plan {
     PrefetchHint* d_hint;         // the same ring as the kernels address it
     // host
     double* h_res;                // pinned copy of d_res
+    double* h_ring[2];            // pinned results of pcal_finalize_async (5N+3 values, then the error word)
+    cudaEvent_t ring_ev[2];       // ring slot i filled
+    int64_t ring_count;           // pcal_finalize_async calls
     void* h_stage[2];             // pinned staging for pcal_accumulate_host
     void* d_stage[2];             // device staging for pcal_accumulate_host
     size_t stage_bytes;

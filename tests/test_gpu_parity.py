@@ -239,6 +239,34 @@ def test_host_accumulate_matches_device(pcal):
     assert np.array_equal(bins_h, oracle.counts_2bit(host, 0, p.L))
 
 
+def test_pipelined_host_periods(pcal):
+    """accumulate_host_async + finalize_async over three periods, each period's results read one call later
+    from the pinned ring (and the last at age 0): every period matches the oracle, and ages outside the ring
+    are refused."""
+    fs, fc, fo = PLANS["c2"]
+    n = 4 * 17_000_003  # two staging chunks and a ragged tail
+    hosts = [synth.Stream(fs=fs, fc=fc, fo=fo, amp=0.02, td=2e-9, seed=60 + k).bits2(k * n, n) for k in range(3)]
+    got = []
+    with pcal.Plan(fs, fc, fo, "2bit") as p:
+        with pytest.raises(pcal.PcalError):
+            p.read_async(0)  # nothing finalized yet
+        for k, h in enumerate(hosts):
+            p.accumulate_host_async(h, n)
+            p.finalize_async()
+            if k:
+                got.append(p.read_async(age=1))
+        got.append(p.read_async(age=0))
+        with pytest.raises(pcal.PcalError):
+            p.read_async(2)
+        L = p.L
+    for k, (h, r) in enumerate(zip(hosts, got)):
+        ref = oracle.tones_from_bins(oracle.bins(h, "2bit", k * n, L), fs, fc, fo)
+        scale = np.max(np.abs(ref))
+        assert np.max(np.abs(r["phasors"] - ref)) <= PHASOR_RTOL * scale, k
+        pr = oracle.products(ref, n, fs, fc, fo)
+        assert abs(r["td"] - pr["td"]) <= 1e-3 * pr["sigma_td"]
+
+
 def test_f32_is_deterministic(pcal):
     fs, fc, fo = PLANS["c1"]
     n = 4_000_000 + 17
