@@ -596,9 +596,13 @@ int bulk_tiling(const pcal_plan* p, int64_t n_rows, BulkTiling* t) {
     int r_max = (kMaxBlock / 32 - 1) / wpr;
     if (r_max > 8) r_max = 8;
     if (r_max < 1) r_max = 1;
-    // a stage of about 24-32 KB; 2-bit boxes are whole 32-row blocks
+    // 2-bit: a stage of about 48-64 KB of whole 32-row blocks (each TMA box
+    // copy costs the producer a fixed ~0.3 us to issue, whatever its size, so
+    // fewer, larger boxes fill the pipeline sooner after a launch: short
+    // launches are 2-bit); int8 / f32: about 24-32 KB, which keeps 2 replica
+    // groups and 8 stages on wide rows
     const int unit = p->g.format == PCAL_2BIT ? 32 : 8;
-    int units = (28 * 1024) / (unit * cw * 4);
+    int units = (p->g.format == PCAL_2BIT ? 56 * 1024 : 28 * 1024) / (unit * cw * 4);
     if (units < 1) units = 1;
     int box = unit * units;
     while (box > 256) box -= unit;
