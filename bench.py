@@ -437,6 +437,9 @@ def run_gpu(args):
             torch.cuda.empty_cache()
             out["tensor_dft"] = summarize_extra(lambda: run_tensor_dft(extra_args(args), emit=False),
                                                 ("modes", "speedup_vs_fp32", "config"))
+            torch.cuda.empty_cache()
+            out["c1_f32"] = summarize_extra(lambda: run_c1(extra_args(args), emit=False),
+                                            ("value", "unit", "ms_per_step", "roofline", "config"))
         print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
@@ -695,6 +698,63 @@ def run_batch(args, emit=True):
             print(json.dumps(out))
         return out
     return None
+
+
+# ---- the small float32 configuration: launch-dominated ------------------------------------
+
+C1_WORKLOAD = ("f32 single channel, fs=16 MHz, f_comb=1 MHz (N=16), f_offset=10 kHz (L=1600), 16M samples (1 s, "
+               "64 MB), Gaussian sigma 1 + 16 tones of amplitude 0.02, t_d 3.7 ns")
+
+
+def run_c1(args, emit=True, n_buffers=8):
+    """C1 step (accumulate 16M float32 samples + finalize) with inputs rotating over 8 device buffers
+    (512 MB > L2); the fold + partial reduction alone timed after it."""
+    import torch
+
+    import paper_2501_05993_gb300 as pcal
+    import synth
+    from paper_2501_05993_gb300 import build as libbuild
+
+    libbuild.build()
+    pcal.load()
+    fs, fc, fo, m = 16_000_000, 1_000_000, 10_000, 16_000_000
+    host = synth.Stream(fs=fs, fc=fc, fo=fo, amp=0.02, td=3.7e-9, seed=2501059930).f32(0, m)
+    src = torch.from_numpy(host).cuda()
+    bufs = [src.clone() for _ in range(n_buffers)]
+    plan = pcal.Plan(fs, fc, fo, "f32")
+    stream = torch.cuda.current_stream()
+    h = plan.handle
+    for i in range(max(args.warmup, 3)):
+        pcal.pcal_accumulate(h, bufs[i % n_buffers], m, stream)
+        pcal.pcal_finalize_device(h, stream)
+    torch.cuda.synchronize()
+    k = max(args.steps, 20)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e[0].record(stream)
+    for i in range(k):
+        pcal.pcal_accumulate(h, bufs[i % n_buffers], m, stream)
+        pcal.pcal_finalize_device(h, stream)
+    e[1].record(stream)
+    for i in range(k):
+        pcal.pcal_accumulate(h, bufs[i % n_buffers], m, stream)
+    e[2].record(stream)
+    torch.cuda.synchronize()
+    step_ms, fold_ms = e[0].elapsed_time(e[1]) / k, e[1].elapsed_time(e[2]) / k
+    res = plan.results()
+    plan.close()
+    peak, peak_kind = read_peaks()
+    nbytes = 4 * m
+    out = {"metric": "PCal Gsamples/s (f32 single-stream extraction: accumulate + finalize)",
+           "value": m / (step_ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": step_ms, "steps": k,
+           "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": C1_WORKLOAD, "fold_ms": fold_ms, "td_s": res["td"], "sigma_td_s": res["sigma_td"],
+                      "l2": f"inputs rotate over {n_buffers} device buffers ({n_buffers * nbytes >> 20} MB) > L2"},
+           "roofline": {"bound": "hbm", "achieved": nbytes / (fold_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                        "frac": nbytes / (fold_ms / 1e3) / 1e9 / peak, "traffic": None,
+                        "peak_kind": f"{peak_kind} (copy bandwidth)", "kernel": "bulk_fold_kernel<f32> + reduce"}}
+    if emit:
+        print(json.dumps(out))
+    return out
 
 
 # ---- batched tone DFT on the tensor cores ------------------------------------------------
@@ -990,7 +1050,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="single workload: skip the batched and serving summaries")
     ap.add_argument("--prec-scale", type=float, default=1.0, help="precision workload: fraction of the 16 s")
     ap.add_argument("--prec-lanes", type=int, default=128)
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "precision", "dft"],
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "precision", "dft", "c1"],
                     help="single: the 2-bit single-channel headline workload; batch: 64 mixed channels")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -1005,6 +1065,8 @@ def main():
         run_precision(args)
     elif args.workload == "dft":
         run_tensor_dft(args)
+    elif args.workload == "c1":
+        run_c1(args)
     else:
         run_gpu(args)
 

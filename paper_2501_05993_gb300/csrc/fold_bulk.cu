@@ -479,6 +479,9 @@ __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_co
         float2* m = reinterpret_cast<float2*>(smem);
         if (active) m[q * a.col_width + col] = make_float2(accf.s, accf.c);
         __syncthreads();
+        // the partials of the previous f32 launch are summed by its reduce
+        // kernel, which may still run: wait for the preceding kernel first
+        grid_dependency_wait();
         if (tid < a.col_width && c0 + tid < a.cols_total) {
             float s = 0.f, c = 0.f;
             for (int r = 0; r < a.replicas; ++r) {
@@ -498,8 +501,12 @@ __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_co
 
 // f32: bin k = sum over row groups and over the columns that map to k, in a
 // fixed order and in double-float, added to the plan's double-float bins.
+// Launched as a programmatic dependent of the fold: it lets the next kernel
+// start launching, then waits for the fold's partials.
 __global__ void reduce_f32_kernel(const float2* __restrict__ part, int64_t row_groups, int cols_total, int64_t k_a,
                                   int64_t L, float2* __restrict__ acc) {
+    allow_dependents();
+    grid_dependency_wait();
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= L) return;
     const int64_t c_first = ((k - k_a) % L + L) % L;
@@ -772,11 +779,20 @@ cudaError_t launch_bulk(pcal_plan* p, const void* d_rows, int64_t n_rows, int64_
             unpublish_hint(p, a.epoch);
             return e;
         }
-        reduce_f32_kernel<<<(unsigned)((p->g.L + 255) / 256), 256, 0, s>>>(p->d_partf, t.row_groups, t.cols_total,
-                                                                           k_a, p->g.L, cur_accf(p));
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)((p->g.L + 255) / 256));
+        cfg.blockDim = dim3(256);
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, reduce_f32_kernel, (const float2*)p->d_partf, (int64_t)t.row_groups,
+                               (int)t.cols_total, (int64_t)k_a, (int64_t)p->g.L, cur_accf(p));
         *launched = 2;
         p->stats.kernel_launches += 2;
-        return cudaGetLastError();
+        return e;
     }
     if (p->g.format == PCAL_I8) {
         e = launch_one<PCAL_I8, 1>(map, a, grid, t.threads, t.smem_bytes, s);
