@@ -2,8 +2,9 @@
 // for C channels at once (the "DFT(P)" step of Sec. 2 after the L-to-N fold of
 // Eq. 2), as one real contraction
 //
-//   [Re T | Im T] (C x 2N) = [Re P | Im P] (C x 2N) . W (2N x 2N),
-//   W = [[ cos, -sin ], [ sin, cos ]] of the angles 2 pi (i b mod N) / N,
+//   T (C x 2N, Re T_i and Im T_i side by side) = [Re P | Im P] (C x 2N) . W,
+//   W (2N x 2N): column 2i = (cos; sin), column 2i + 1 = (-sin; cos) of the
+//   angles 2 pi (i b mod N) / N (rows b < N for Re P, then Im P),
 //
 // which is dense, so it belongs on the tensor cores.  The operands are split
 // in two parts of the MMA type (x = hi + lo, hi = round(x), lo = round(x - hi))
@@ -111,13 +112,15 @@ __host__ __device__ constexpr int esize_of() {
 
 // Element W[n][k] of the transposed weight matrix (row n = output column,
 // k = contraction index) from the FP64 twiddles tw[m] = e^{-j 2 pi m/N}.
+// Output columns interleave the parts of each tone (column 2i = Re T_i,
+// 2i + 1 = Im T_i), so a tile's row is a contiguous run of complex T.
 inline double weight(const double* twr, const double* twi, int N, int n, int k) {
-    const int i = n < N ? n : n - N;      // tone
+    const int i = n / 2;                  // tone
     const int b = k < N ? k : k - N;      // residue
     const int m = (int)(((int64_t)i * b) % N);
     const double c = twr[m], s = twi[m];  // e^{-j theta} = c + j s, s = -sin
-    if (n < N) return k < N ? c : -s;     // Re T = Re P cos + Im P sin
-    return k < N ? s : c;                 // Im T = -Re P sin + Im P cos
+    if (n % 2 == 0) return k < N ? c : -s;  // Re T = Re P cos + Im P sin
+    return k < N ? s : c;                   // Im T = -Re P sin + Im P cos
 }
 
 // ---- device side ------------------------------------------------------------
@@ -200,36 +203,55 @@ struct DftTcArgs {
     int n_cols;        // 2N rounded up to 16
     int k_chunks;      // chunks of K = 2N
     const uint8_t* a;  // operand tiles of P: [row tile][chunk] x (hi, lo) x kATile bytes
-    const uint8_t* w;  // weight tiles: [column tile][chunk] x (hi, lo) x kBTile bytes
+    const uint8_t* w;  // weight tiles: [column tile][chunk] x 2 kBTile bytes: hi rows, then lo rows
     unsigned int* err;
 };
 
 // P -> split operand tiles: row tile mt, chunk kc holds rows 128 mt.. and K
 // values kc*KC.. of [Re P | Im P] (zeros past C and 2N) as hi and lo tile
-// images.  One thread per (row, K value).
+// images.  One thread per 16-byte row segment of a core matrix (8 BF16 or
+// 4 TF32 values): consecutive threads take consecutive rows, so eight of
+// them fill one 128-byte core matrix and the stores coalesce.
 template <int MODE>
 __global__ void split_p_kernel(const float2* __restrict__ P, int64_t C, int N, int k_chunks, uint8_t* __restrict__ out,
                                int64_t total) {
     constexpr int ES = esize_of<MODE>();
-    constexpr int KC = kChunkBytes / ES;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        // e = ((mt * k_chunks + kc) * 128 + r) * KC + k
-        const int k = (int)(e % KC);
-        const int64_t rest = e / KC;
-        const int r = (int)(rest % kTcM);
-        const int64_t blk = rest / kTcM;
+    constexpr int V = 16 / ES;              // values per segment
+    constexpr int SEGS = kChunkBytes / 16;  // segments per row and chunk
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+        // g = (blk * SEGS + sg) * 128 + r
+        const int r = (int)(g % kTcM);
+        const int64_t rest = g / kTcM;
+        const int sg = (int)(rest % SEGS);
+        const int64_t blk = rest / SEGS;
         const int kc = (int)(blk % k_chunks);
-        const int64_t mt = blk / k_chunks;
-        const int64_t c = mt * kTcM + r;
-        const int kk = kc * KC + k;
-        float x = 0.f;
-        if (c < C && kk < 2 * N) {
-            const float2 v = P[c * N + (kk < N ? kk : kk - N)];
-            x = kk < N ? v.x : v.y;
+        const int64_t c = (blk / k_chunks) * kTcM + r;
+        const int kk0 = kc * (kChunkBytes / ES) + sg * V;
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int w = 0; w < 4; ++w) h[w] = l[w] = 0;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const int kk = kk0 + v;
+            float x = 0.f;
+            if (c < C && kk < 2 * N) {
+                const float2 pv = P[c * N + (kk < N ? kk : kk - N)];
+                x = kk < N ? pv.x : pv.y;
+            }
+            if (MODE == PCAL_DFT_TC_TF32X3) {
+                h[v] = tf32_bits_rna(x);
+                l[v] = tf32_bits_rna(x - f32_of_bits(h[v]));
+            } else {
+                const uint32_t hb = bf16_bits_rn(x);
+                const uint32_t lb = bf16_bits_rn(x - f32_of_bits(hb << 16));
+                h[v / 2] |= hb << (16 * (v & 1));
+                l[v / 2] |= lb << (16 * (v & 1));
+            }
         }
         uint8_t* base = out + (size_t)blk * 2 * kATile;
-        const uint32_t o = tile_offset(r, k, kTcM, ES);
-        split_store<MODE>(x, base + o, base + kATile + o);
+        const uint32_t o = tile_offset(r, sg * V, kTcM, ES);  // 16-byte aligned
+        *reinterpret_cast<uint4*>(base + o) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4*>(base + kATile + o) = make_uint4(l[0], l[1], l[2], l[3]);
     }
 }
 
@@ -290,8 +312,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) dft_tc_kernel(const DftTcArgs a
             uint8_t* st = smem + (size_t)s * kStageBytes;
             mbar_arrive_expect_tx(&full[s], 2 * kATile + 2 * w_bytes);
             bulk_load(st, atile + (size_t)kc * 2 * kATile, 2 * kATile, &full[s]);
-            bulk_load(st + 2 * kATile, wtile + (size_t)kc * 2 * kBTile, w_bytes, &full[s]);
-            bulk_load(st + 2 * kATile + kBTile, wtile + (size_t)kc * 2 * kBTile + kBTile, w_bytes, &full[s]);
+            bulk_load(st + 2 * kATile, wtile + (size_t)kc * 2 * kBTile, 2 * w_bytes, &full[s]);  // hi and lo
         }
         if (s_fail) {
             // copies in flight must land before the CTA's shared memory is reused
@@ -313,7 +334,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) dft_tc_kernel(const DftTcArgs a
             }
             tc_fence_after();
             const uint32_t st = smem_addr(smem + (size_t)s * kStageBytes);
-            const uint32_t a_hi = st, a_lo = st + kATile, b_hi = st + 2 * kATile, b_lo = st + 2 * kATile + kBTile;
+            const uint32_t a_hi = st, a_lo = st + kATile, b_hi = st + 2 * kATile, b_lo = b_hi + w_bytes;
             // hi.hi: even / odd chunks; cross products: one accumulator
             const uint32_t d_hh = tmem + (uint32_t)(kc & 1) * kTcNMax, d_x = tmem + 2 * kTcNMax;
 #pragma unroll
@@ -331,14 +352,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) dft_tc_kernel(const DftTcArgs a
     }
     // every thread: wait for the last MMAs (the issuer committed `done`)
     __syncthreads();
-    const bool have = !s_fail && mbar_wait(&done, 0);
+    const bool have = __syncthreads_and(!s_fail && mbar_wait(&done, 0)) != 0;  // uniform over the CTA
     if (!have && tid == 0) atomicOr(a.err, PCAL_DERR_DRAIN_WAIT);
     tc_fence_after();
     if (have) {
         // epilogue: warp w reads TMEM lanes 32 (w % 4) .. (rows), column half
-        // w / 4, and adds the three accumulators
+        // w / 4, adds the three accumulators and parks the rows in shared
+        // memory (the stages are free; row stride 129 floats: no bank
+        // conflicts), then all threads write the tile's rows of complex T,
+        // consecutive threads on consecutive tones.
+        constexpr int kRow = kTcNMax + 1;
+        float* sT = reinterpret_cast<float*>(smem);
         const int q = warp & 3, half = warp >> 2;
-        const int64_t c = m0 + 32 * q + (tid & 31);
+        const int r = 32 * q + (tid & 31);
         const uint32_t lane = (uint32_t)(32 * q) << 16;
         for (int j0 = half * (kTcNMax / 2); j0 < nt && j0 < (half + 1) * (kTcNMax / 2); j0 += 8) {
             float v[8], w[8], x[8];
@@ -350,17 +376,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) dft_tc_kernel(const DftTcArgs a
                 for (int u = 0; u < 8; ++u) v[u] += w[u];
             }
 #pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] += x[u];
-            if (c < a.C) {
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int n = n0 + j0 + u;
-                    if (n < a.N)
-                        a.T[c * a.N + n].x = v[u];
-                    else if (n < 2 * a.N)
-                        a.T[c * a.N + (n - a.N)].y = v[u];
-                }
-            }
+            for (int u = 0; u < 8; ++u) sT[r * kRow + j0 + u] = v[u] + x[u];
+        }
+        __syncthreads();
+        const int tones = nt / 2, t0 = n0 / 2;
+        for (int e = tid; e < kTcM * tones; e += kTcThreads) {
+            const int rr = e / tones, i = e % tones;
+            const int64_t c = m0 + rr;
+            if (c < a.C && t0 + i < a.N)
+                a.T[c * a.N + t0 + i] = make_float2(sT[rr * kRow + 2 * i], sT[rr * kRow + 2 * i + 1]);
         }
     }
     tc_fence_before();
@@ -494,8 +518,10 @@ extern "C" int pcal_dft_create(int N, int mode, pcal_dft** out) {
         if (!h) e = cudaErrorMemoryAllocation;
         for (int t = 0; h && t < d->col_tiles; ++t)
             for (int kc = 0; kc < d->k_chunks; ++kc) {
+                // hi rows, then the lo rows right after them: one copy per chunk
                 uint8_t* base = h + ((size_t)t * d->k_chunks + kc) * 2 * kBTile;
-                build_weight_tile(N, mode, t, kc, tw, tw + N, base, base + kBTile);
+                const int rows = build_weight_tile(N, mode, t, kc, tw, tw + N, base, base + kBTile);
+                if (rows < kTcNMax) memmove(base + (size_t)rows * kChunkBytes, base + kBTile, (size_t)rows * kChunkBytes);
             }
         if (e == cudaSuccess) e = cudaMalloc(&d->d_w, bytes);
         if (e == cudaSuccess) e = cudaMemcpy(d->d_w, h, bytes, cudaMemcpyHostToDevice);
@@ -551,7 +577,7 @@ cudaError_t launch_dft(pcal_dft* d, const float2* P, int64_t C, float2* T, cudaS
     }
     const int64_t m_tiles = (C + kTcM - 1) / kTcM;
     if ((size_t)m_tiles * d->k_chunks * 2 * kATile > d->a_cap) return cudaErrorInvalidValue;  // dft_reserve first
-    const int64_t total = m_tiles * d->k_chunks * kTcM * (kChunkBytes / (d->mode == PCAL_DFT_TC_TF32X3 ? 4 : 2));
+    const int64_t total = m_tiles * d->k_chunks * kTcM * (kChunkBytes / 16);  // 16-byte segments
     const int sgrid = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
     if (d->mode == PCAL_DFT_TC_TF32X3)
         split_p_kernel<PCAL_DFT_TC_TF32X3><<<sgrid, 256, 0, s>>>(P, C, d->N, d->k_chunks, d->d_a, total);

@@ -1,8 +1,8 @@
 """Host checks of the tensor-core DFT's weight tiles (no GPU).
 
 The tiles hold W^T of the real form of the tone DFT, T = [Re P | Im P] . W with
-W = [[cos, -sin], [sin, cos]] (angles 2 pi (i b mod N) / N), each value split in
-two parts of the MMA type.  Decoding a tile with the no-swizzle K-major layout
+Re T_i and Im T_i in output columns 2i and 2i + 1 (angles 2 pi (i b mod N) / N),
+each value split in two parts of the MMA type.  Decoding a tile with the no-swizzle K-major layout
 (8-row x 16-byte core matrices, K-neighbours rows/8 * 128 bytes apart, 8-row
 bands 128 bytes apart) must give back the matrix entries to the precision of the
 split, and zeros in the padding.
@@ -39,12 +39,13 @@ def decode(tile: np.ndarray, rows: int, esize: int) -> np.ndarray:
 
 
 def expected(N: int, n: np.ndarray, k: np.ndarray) -> np.ndarray:
-    """W^T[n, k] of the real-form DFT, with zeros outside 2N x 2N."""
-    i = np.where(n < N, n, n - N)
+    """W^T[n, k] of the real-form DFT (output column 2i = Re T_i, 2i + 1 = Im T_i; contraction index k < N for
+    Re P[k], k >= N for Im P[k - N]), with zeros outside 2N x 2N."""
+    i = n // 2
     b = np.where(k < N, k, k - N)
     th = 2 * np.pi * ((i * b) % N) / N
     c, s = np.cos(th), -np.sin(th)  # e^{-j th} = c + j s
-    w = np.where(n < N, np.where(k < N, c, -s), np.where(k < N, s, c))
+    w = np.where(n % 2 == 0, np.where(k < N, c, -s), np.where(k < N, s, c))
     return np.where((n < 2 * N) & (k < 2 * N), w, 0.0)
 
 
