@@ -120,6 +120,14 @@ struct IterInfo;
 
 }  // namespace
 
+// One piece of a submit's ingest: bytes from host memory the GPU can read
+// into a stream's ring.
+struct CopyPiece {
+    const uint8_t* src;
+    uint8_t* dst;
+    long long bytes;
+};
+
 struct pcal_server {
     pcal_server_config cfg;
     int device = 0, num_sms = 0;
@@ -142,6 +150,13 @@ struct pcal_server {
     int desc_next = 0;
     unsigned long long* d_ctr = nullptr;
     unsigned int* d_err = nullptr;
+    // ingest: host chunks the GPU can read are gathered by one kernel per
+    // submit (hundreds of small copies cost the copy engine more than the
+    // link); the piece list lives in pinned, mapped memory
+    int pageable_access = 0;          // the device reads pageable host memory
+    CopyPiece* h_pieces = nullptr;
+    CopyPiece* d_pieces = nullptr;
+    int pieces_cap = 0;
     // threads
     std::mutex mu;
     std::mutex copy_mu;
@@ -157,6 +172,48 @@ struct pcal_server {
 };
 
 namespace {
+
+constexpr long long kPieceBytes = 256 << 10;  // gather work unit
+
+// Block b copies pieces b, b + gridDim.x, ...: 16-byte words when the piece
+// is 16-byte aligned at both ends and in length, bytes otherwise.  The host
+// memory reads are issued four at a time per thread to keep the link busy.
+__global__ void gather_kernel(const CopyPiece* __restrict__ pieces, int n) {
+    for (int b = blockIdx.x; b < n; b += gridDim.x) {
+        const CopyPiece p = pieces[b];
+        const uintptr_t al = reinterpret_cast<uintptr_t>(p.src) | reinterpret_cast<uintptr_t>(p.dst) |
+                             static_cast<uintptr_t>(p.bytes);
+        if ((al & 15) == 0) {
+            const uint4* src = reinterpret_cast<const uint4*>(p.src);
+            uint4* dst = reinterpret_cast<uint4*>(p.dst);
+            const long long n16 = p.bytes / 16, step = 4ll * blockDim.x;
+            for (long long i = threadIdx.x; i < n16; i += step) {
+                uint4 v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (i + u * blockDim.x < n16) v[u] = src[i + u * blockDim.x];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (i + u * blockDim.x < n16) dst[i + u * blockDim.x] = v[u];
+            }
+        } else {
+            for (long long i = threadIdx.x; i < p.bytes; i += blockDim.x) p.dst[i] = p.src[i];
+        }
+    }
+}
+
+// Address through which the device reads host buffer `p`, or null when it
+// cannot (pageable memory without pageable-memory access).
+const uint8_t* device_view(const pcal_server* s, const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return s->pageable_access ? static_cast<const uint8_t*>(p) : nullptr;
+    }
+    if (at.type == cudaMemoryTypeHost && at.devicePointer) return static_cast<const uint8_t*>(at.devicePointer);
+    if (at.type == cudaMemoryTypeUnregistered && s->pageable_access) return static_cast<const uint8_t*>(p);
+    return nullptr;
+}
 
 struct IterInfo {
     pcal_server* s;
@@ -398,6 +455,11 @@ extern "C" int pcal_server_create(const pcal_server_config* cfg, pcal_server** o
     if (e == cudaSuccess) e = cudaMemset(s->d_err, 0, 256);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking);
+    if (e == cudaSuccess &&
+        cudaDeviceGetAttribute(&s->pageable_access, cudaDevAttrPageableMemoryAccess, s->device) != cudaSuccess) {
+        (void)cudaGetLastError();
+        s->pageable_access = 0;
+    }
     for (int k = 0; k < kSlots && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&s->desc_ev[k], cudaEventDisableTiming);
     if (e == cudaSuccess) e = batch_prepare_fold();
     if (e == cudaSuccess) e = prepare_batch_finalize();
@@ -432,6 +494,8 @@ extern "C" int pcal_server_destroy(pcal_server* s) {
         if (s->d_desc[k]) cudaFree(s->d_desc[k]);
         if (s->desc_ev[k]) cudaEventDestroy(s->desc_ev[k]);
     }
+    if (s->copy) cudaStreamSynchronize(s->copy);
+    if (s->h_pieces) cudaFreeHost(s->h_pieces);
     if (s->compute) cudaStreamDestroy(s->compute);
     if (s->copy) cudaStreamDestroy(s->copy);
     cudaFree(s->d_mem);
@@ -514,22 +578,49 @@ extern "C" int pcal_server_submit_many(pcal_server* s, int count, const int* ids
             pos[k] = st.submitted;
         }
     }
-    // copy into the rings (split where a ring wraps), then wait for the copies
+    // copy into the rings (split where a ring wraps), then wait for the copies:
+    // chunks the device can read go to one gather launch, the others to the
+    // copy engine
     int64_t bytes = 0;
     {
         std::lock_guard<std::mutex> cl(s->copy_mu);
         cudaError_t e = cudaSuccess;
+        std::vector<CopyPiece> pieces;
         for (int k = 0; k < count && e == cudaSuccess; ++k) {
             SrvStream& st = s->streams[ids[k]];
             const uint8_t* src = static_cast<const uint8_t*>(host[k]);
+            const uint8_t* view = n[k] > 0 ? device_view(s, src) : nullptr;
             int64_t nb = n[k] / st.spb, b0 = (pos[k] / st.spb) % st.ring_bytes;
             bytes += nb;
             while (nb > 0 && e == cudaSuccess) {
                 const int64_t take = std::min(nb, st.ring_bytes - b0);
-                e = cudaMemcpyAsync(st.ring + b0, src, take, cudaMemcpyHostToDevice, s->copy);
+                if (view) {
+                    for (int64_t o = 0; o < take; o += kPieceBytes)
+                        pieces.push_back(CopyPiece{view + o, st.ring + b0 + o, std::min<int64_t>(kPieceBytes, take - o)});
+                    view += take;
+                } else {
+                    e = cudaMemcpyAsync(st.ring + b0, src, take, cudaMemcpyHostToDevice, s->copy);
+                }
                 src += take;
                 nb -= take;
                 b0 = 0;
+            }
+        }
+        if (e == cudaSuccess && !pieces.empty()) {
+            if ((int)pieces.size() > s->pieces_cap) {
+                if (s->h_pieces) cudaFreeHost(s->h_pieces);
+                s->h_pieces = nullptr;
+                s->pieces_cap = 0;
+                const int cap = (int)pieces.size() * 2;
+                e = cudaHostAlloc(reinterpret_cast<void**>(&s->h_pieces), sizeof(CopyPiece) * cap, cudaHostAllocMapped);
+                if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->d_pieces), s->h_pieces, 0);
+                if (e == cudaSuccess) s->pieces_cap = cap;
+            }
+            if (e == cudaSuccess) {
+                memcpy(s->h_pieces, pieces.data(), sizeof(CopyPiece) * pieces.size());
+                const int grid = std::min<int>((int)pieces.size(), 4 * s->num_sms);
+                gather_kernel<<<grid, 256, 0, s->copy>>>(s->d_pieces, (int)pieces.size());
+                e = cudaGetLastError();
             }
         }
         if (e == cudaSuccess) e = cudaStreamSynchronize(s->copy);
