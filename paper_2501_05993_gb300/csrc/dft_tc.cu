@@ -209,49 +209,35 @@ struct DftTcArgs {
 
 // P -> split operand tiles: row tile mt, chunk kc holds rows 128 mt.. and K
 // values kc*KC.. of [Re P | Im P] (zeros past C and 2N) as hi and lo tile
-// images.  One thread per 16-byte row segment of a core matrix (8 BF16 or
-// 4 TF32 values): consecutive threads take consecutive rows, so eight of
-// them fill one 128-byte core matrix and the stores coalesce.
+// images.  One block per tile: the threads read P along K (consecutive
+// threads, consecutive values of a row), build the two images in shared
+// memory, then store them as contiguous 16-byte words.
 template <int MODE>
-__global__ void split_p_kernel(const float2* __restrict__ P, int64_t C, int N, int k_chunks, uint8_t* __restrict__ out,
-                               int64_t total) {
+__global__ void __launch_bounds__(256) split_p_kernel(const float2* __restrict__ P, int64_t C, int N, int k_chunks,
+                                                      uint8_t* __restrict__ out, int64_t tiles) {
     constexpr int ES = esize_of<MODE>();
-    constexpr int V = 16 / ES;              // values per segment
-    constexpr int SEGS = kChunkBytes / 16;  // segments per row and chunk
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
-        // g = (blk * SEGS + sg) * 128 + r
-        const int r = (int)(g % kTcM);
-        const int64_t rest = g / kTcM;
-        const int sg = (int)(rest % SEGS);
-        const int64_t blk = rest / SEGS;
+    constexpr int KC = kChunkBytes / ES;
+    __shared__ __align__(16) uint8_t img[2 * kATile];
+    for (int64_t blk = blockIdx.x; blk < tiles; blk += gridDim.x) {
         const int kc = (int)(blk % k_chunks);
-        const int64_t c = (blk / k_chunks) * kTcM + r;
-        const int kk0 = kc * (kChunkBytes / ES) + sg * V;
-        uint32_t h[4], l[4];
-#pragma unroll
-        for (int w = 0; w < 4; ++w) h[w] = l[w] = 0;
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            const int kk = kk0 + v;
+        const int64_t m0 = (blk / k_chunks) * kTcM;
+        for (int e = threadIdx.x; e < kTcM * KC; e += blockDim.x) {
+            const int r = e / KC, k = e % KC;
+            const int64_t c = m0 + r;
+            const int kk = kc * KC + k;
             float x = 0.f;
             if (c < C && kk < 2 * N) {
                 const float2 pv = P[c * N + (kk < N ? kk : kk - N)];
                 x = kk < N ? pv.x : pv.y;
             }
-            if (MODE == PCAL_DFT_TC_TF32X3) {
-                h[v] = tf32_bits_rna(x);
-                l[v] = tf32_bits_rna(x - f32_of_bits(h[v]));
-            } else {
-                const uint32_t hb = bf16_bits_rn(x);
-                const uint32_t lb = bf16_bits_rn(x - f32_of_bits(hb << 16));
-                h[v / 2] |= hb << (16 * (v & 1));
-                l[v / 2] |= lb << (16 * (v & 1));
-            }
+            const uint32_t o = tile_offset(r, k, kTcM, ES);
+            split_store<MODE>(x, img + o, img + kATile + o);
         }
-        uint8_t* base = out + (size_t)blk * 2 * kATile;
-        const uint32_t o = tile_offset(r, sg * V, kTcM, ES);  // 16-byte aligned
-        *reinterpret_cast<uint4*>(base + o) = make_uint4(h[0], h[1], h[2], h[3]);
-        *reinterpret_cast<uint4*>(base + kATile + o) = make_uint4(l[0], l[1], l[2], l[3]);
+        __syncthreads();
+        uint4* dst = reinterpret_cast<uint4*>(out + (size_t)blk * 2 * kATile);
+        const uint4* src = reinterpret_cast<const uint4*>(img);
+        for (int i = threadIdx.x; i < 2 * kATile / 16; i += blockDim.x) dst[i] = src[i];
+        __syncthreads();
     }
 }
 
@@ -577,8 +563,8 @@ cudaError_t launch_dft(pcal_dft* d, const float2* P, int64_t C, float2* T, cudaS
     }
     const int64_t m_tiles = (C + kTcM - 1) / kTcM;
     if ((size_t)m_tiles * d->k_chunks * 2 * kATile > d->a_cap) return cudaErrorInvalidValue;  // dft_reserve first
-    const int64_t total = m_tiles * d->k_chunks * kTcM * (kChunkBytes / 16);  // 16-byte segments
-    const int sgrid = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+    const int64_t total = m_tiles * d->k_chunks;  // tiles
+    const int sgrid = (int)(total < 8 * 152 ? total : 8 * 152);
     if (d->mode == PCAL_DFT_TC_TF32X3)
         split_p_kernel<PCAL_DFT_TC_TF32X3><<<sgrid, 256, 0, s>>>(P, C, d->N, d->k_chunks, d->d_a, total);
     else
