@@ -829,8 +829,8 @@ class Dft:
 
 
 def pcal_dft_weights_host(N: int, mode: str, tile: int, chunk: int) -> tuple[np.ndarray, np.ndarray, int]:
-    """Host copy of the hi and lo weight tiles (tile, chunk) of a tensor-core mode (16 KB each)."""
-    hi, lo = np.zeros(16384, np.uint8), np.zeros(16384, np.uint8)
+    """Host copy of the hi and lo weight tiles (tile, chunk) of a tensor-core mode (up to 32 KB each)."""
+    hi, lo = np.zeros(32768, np.uint8), np.zeros(32768, np.uint8)
     rows = ctypes.c_int()
     _check(load().pcal_dft_weights_host(int(N), DFT_MODES[mode], int(tile), int(chunk), hi.ctypes.data,
                                         lo.ctypes.data, ctypes.byref(rows)), "pcal_dft_weights_host")

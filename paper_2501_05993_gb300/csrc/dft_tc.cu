@@ -15,8 +15,8 @@
 // accumulators (even and odd K chunks) and the small cross products to a
 // third, and the three are added in FP32 at the end (error figures: pcal.h).
 //
-// Tiles.  A CTA owns 128 channels (MMA M, rows in TMEM lanes) x up to 128
-// output columns (MMA N; three accumulators of 128 TMEM columns) and walks
+// Tiles.  A CTA owns 128 channels (MMA M, rows in TMEM lanes) x up to 256
+// (split BF16) or 128 (split TF32) output columns (MMA N) and walks
 // K = 2N in chunks of 128 bytes per row (32 TF32 or 64 BF16 values).  Per
 // chunk it converts its rows of P into the hi/lo A tiles in shared memory
 // while one 1-D bulk copy brings the chunk's precomputed hi/lo W tiles, then
@@ -38,12 +38,25 @@ namespace {
 using namespace pcal_ptx;
 
 constexpr int kTcM = 128;              // channels per tile (MMA M)
-constexpr int kTcNMax = 128;           // output columns per tile (MMA N)
+// Output columns per tile (MMA N), stages and accumulators per mode: split
+// BF16 (16 K values per MMA) takes 256-column tiles with two accumulators
+// (hi.hi, cross products) in 2 stages of 96 KB; split TF32 (8 K values per
+// MMA, twice the MMAs per accumulator) 128-column tiles with the hi.hi
+// products over even and odd chunks in separate accumulators, in 3 stages
+// of 64 KB.
+template <int MODE>
+struct TcCfg {
+    static constexpr bool kWide = MODE == PCAL_DFT_TC_BF16X3;
+    static constexpr int kNT = kWide ? 256 : 128;
+    static constexpr int kStages = kWide ? 2 : 3;
+    static constexpr int kBTile = kNT * 128;                     // bytes of one weight part per chunk
+    static constexpr int kStageBytes = 2 * 128 * 128 + 2 * kBTile;  // A hi, A lo, B hi, B lo
+    static constexpr int kSmem = kStages * kStageBytes;          // 192 KB either way: one CTA per SM
+};
 constexpr int kTcThreads = 256;        // 8 warps
 constexpr int kChunkBytes = 128;       // bytes of K per row and chunk
 constexpr int kATile = kTcM * kChunkBytes;      // 16 KB
-constexpr int kBTile = kTcNMax * kChunkBytes;   // 16 KB
-constexpr int kTmemCols = 512;                  // three accumulators of kTcNMax columns (a power of two)
+constexpr int kTmemCols = 512;                  // the accumulators of either mode (a power of two)
 
 // Byte offset of element (r, k) of a rows x (128 bytes of K) tile, elements
 // of `esize` bytes, in the no-swizzle K-major core-matrix layout.
@@ -241,9 +254,6 @@ __global__ void __launch_bounds__(256) split_p_kernel(const float2* __restrict__
     }
 }
 
-constexpr int kStages = 3;
-constexpr int kStageBytes = 2 * kATile + 2 * kBTile;  // A hi, A lo, B hi, B lo: 64 KB
-constexpr int kSmemTiles = kStages * kStageBytes;      // 192 KB: one CTA (and its 512 TMEM columns) per SM
 
 // One CTA: 128 channels x up to 128 output columns.  Thread 0 streams the A
 // and B tile pairs of each chunk through kStages shared-memory stages (bulk
@@ -255,6 +265,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) dft_tc_kernel(const DftTcArgs a
     constexpr int ES = esize_of<MODE>();
     constexpr int KC = kChunkBytes / ES;  // K values per chunk
     constexpr int KS = 32 / ES;           // K values per MMA
+    using Cfg = TcCfg<MODE>;
+    constexpr int kTcNMax = Cfg::kNT, kStages = Cfg::kStages, kBTile = Cfg::kBTile, kStageBytes = Cfg::kStageBytes;
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
     __shared__ uint32_t s_tmem;
@@ -321,14 +333,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) dft_tc_kernel(const DftTcArgs a
             tc_fence_after();
             const uint32_t st = smem_addr(smem + (size_t)s * kStageBytes);
             const uint32_t a_hi = st, a_lo = st + kATile, b_hi = st + 2 * kATile, b_lo = b_hi + w_bytes;
-            // hi.hi: even / odd chunks; cross products: one accumulator
-            const uint32_t d_hh = tmem + (uint32_t)(kc & 1) * kTcNMax, d_x = tmem + 2 * kTcNMax;
+            // hi.hi: one accumulator (wide tiles) or even / odd chunks; cross
+            // products: the last accumulator
+            const uint32_t d_hh = tmem + (Cfg::kWide ? 0u : (uint32_t)(kc & 1) * kTcNMax);
+            const uint32_t d_x = tmem + (Cfg::kWide ? 1u : 2u) * kTcNMax;
+            const bool hh_first = Cfg::kWide ? kc == 0 : kc < 2;
 #pragma unroll
             for (int k = 0; k < KC / KS; ++k) {
                 const uint32_t oa = (uint32_t)k * 2 * lbo_a, ob = (uint32_t)k * 2 * lbo_b;
                 const uint64_t ah = smem_desc(a_hi + oa, lbo_a, 128), al = smem_desc(a_lo + oa, lbo_a, 128);
                 const uint64_t bh = smem_desc(b_hi + ob, lbo_b, 128), bl = smem_desc(b_lo + ob, lbo_b, 128);
-                tc_mma<MODE>(d_hh, ah, bh, idesc, (kc < 2 && k == 0) ? 0u : 1u);
+                tc_mma<MODE>(d_hh, ah, bh, idesc, (hh_first && k == 0) ? 0u : 1u);
                 tc_mma<MODE>(d_x, ah, bl, idesc, (kc == 0 && k == 0) ? 0u : 1u);
                 tc_mma<MODE>(d_x, al, bh, idesc, 1u);
             }
@@ -355,8 +370,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) dft_tc_kernel(const DftTcArgs a
         for (int j0 = half * (kTcNMax / 2); j0 < nt && j0 < (half + 1) * (kTcNMax / 2); j0 += 8) {
             float v[8], w[8], x[8];
             tc_ld8(tmem + lane + (uint32_t)j0, v);
-            tc_ld8(tmem + lane + (uint32_t)(2 * kTcNMax + j0), x);
-            if (a.k_chunks > 1) {
+            tc_ld8(tmem + lane + (uint32_t)((Cfg::kWide ? 1 : 2) * kTcNMax + j0), x);
+            if (!Cfg::kWide && a.k_chunks > 1) {
                 tc_ld8(tmem + lane + (uint32_t)(kTcNMax + j0), w);
 #pragma unroll
                 for (int u = 0; u < 8; ++u) v[u] += w[u];
@@ -421,11 +436,16 @@ namespace {
 
 // Weight tiles of column tile t, chunk kc, in the shared-memory image the
 // kernel copies (rows = the tile's columns, 128 bytes of K per row).
+inline int tile_cols(int mode) {
+    return mode == PCAL_DFT_TC_TF32X3 ? TcCfg<PCAL_DFT_TC_TF32X3>::kNT : TcCfg<PCAL_DFT_TC_BF16X3>::kNT;
+}
+
 int build_weight_tile(int N, int mode, int t, int kc, const double* twr, const double* twi, uint8_t* hi,
                       uint8_t* lo) {
     const int n_cols = (2 * N + 15) / 16 * 16;
-    const int n0 = t * kTcNMax;
-    const int nt = n_cols - n0 < kTcNMax ? n_cols - n0 : kTcNMax;
+    const int NT = tile_cols(mode);
+    const int n0 = t * NT;
+    const int nt = n_cols - n0 < NT ? n_cols - n0 : NT;
     const int es = mode == PCAL_DFT_TC_TF32X3 ? 4 : 2;
     const int kcv = kChunkBytes / es;
     memset(hi, 0, (size_t)nt * kChunkBytes);
@@ -462,7 +482,7 @@ extern "C" int pcal_dft_weights_host(int N, int mode, int tile, int chunk, void*
     const int n_cols = (2 * N + 15) / 16 * 16;
     const int es = mode == PCAL_DFT_TC_TF32X3 ? 4 : 2;
     const int k_chunks = (2 * N + kChunkBytes / es - 1) / (kChunkBytes / es);
-    if (tile < 0 || tile * kTcNMax >= n_cols || chunk < 0 || chunk >= k_chunks) return PCAL_EINVAL;
+    if (tile < 0 || tile * tile_cols(mode) >= n_cols || chunk < 0 || chunk >= k_chunks) return PCAL_EINVAL;
     double* tw = new (std::nothrow) double[2 * (size_t)N];
     if (!tw) return PCAL_ENOMEM;
     twiddles(N, tw, tw + N);
@@ -480,7 +500,7 @@ extern "C" int pcal_dft_create(int N, int mode, pcal_dft** out) {
     d->N = N;
     d->mode = mode;
     d->n_cols = (2 * N + 15) / 16 * 16;
-    d->col_tiles = (d->n_cols + kTcNMax - 1) / kTcNMax;
+    d->col_tiles = mode == PCAL_DFT_FP32 ? 0 : (d->n_cols + tile_cols(mode) - 1) / tile_cols(mode);
     const int es = mode == PCAL_DFT_TC_TF32X3 ? 4 : 2;
     d->k_chunks = (2 * N + kChunkBytes / es - 1) / (kChunkBytes / es);
     double* tw = new (std::nothrow) double[2 * (size_t)N];
@@ -499,6 +519,7 @@ extern "C" int pcal_dft_create(int N, int mode, pcal_dft** out) {
         if (e == cudaSuccess) e = cudaMemcpy(d->d_tw, h, N * sizeof(float2), cudaMemcpyHostToDevice);
         delete[] h;
     } else if (e == cudaSuccess) {
+        const int NT = tile_cols(mode), kBTile = NT * kChunkBytes;
         const size_t bytes = (size_t)d->col_tiles * d->k_chunks * 2 * kBTile;
         uint8_t* h = new (std::nothrow) uint8_t[bytes];
         if (!h) e = cudaErrorMemoryAllocation;
@@ -507,7 +528,7 @@ extern "C" int pcal_dft_create(int N, int mode, pcal_dft** out) {
                 // hi rows, then the lo rows right after them: one copy per chunk
                 uint8_t* base = h + ((size_t)t * d->k_chunks + kc) * 2 * kBTile;
                 const int rows = build_weight_tile(N, mode, t, kc, tw, tw + N, base, base + kBTile);
-                if (rows < kTcNMax) memmove(base + (size_t)rows * kChunkBytes, base + kBTile, (size_t)rows * kChunkBytes);
+                if (rows < NT) memmove(base + (size_t)rows * kChunkBytes, base + kBTile, (size_t)rows * kChunkBytes);
             }
         if (e == cudaSuccess) e = cudaMalloc(&d->d_w, bytes);
         if (e == cudaSuccess) e = cudaMemcpy(d->d_w, h, bytes, cudaMemcpyHostToDevice);
@@ -515,7 +536,8 @@ extern "C" int pcal_dft_create(int N, int mode, pcal_dft** out) {
     }
     delete[] tw;
     if (e == cudaSuccess && mode != PCAL_DFT_FP32) {
-        const int smem = kSmemTiles;
+        const int smem = TcCfg<PCAL_DFT_TC_TF32X3>::kSmem;
+        static_assert(TcCfg<PCAL_DFT_TC_TF32X3>::kSmem == TcCfg<PCAL_DFT_TC_BF16X3>::kSmem, "one attribute value");
         e = mode == PCAL_DFT_TC_TF32X3
                 ? cudaFuncSetAttribute(dft_tc_kernel<PCAL_DFT_TC_TF32X3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        smem)
@@ -580,9 +602,9 @@ cudaError_t launch_dft(pcal_dft* d, const float2* P, int64_t C, float2* T, cudaS
     a.err = err ? err : d->d_err;
     const dim3 grid((unsigned)m_tiles, (unsigned)d->col_tiles);
     if (d->mode == PCAL_DFT_TC_TF32X3)
-        dft_tc_kernel<PCAL_DFT_TC_TF32X3><<<grid, kTcThreads, kSmemTiles, s>>>(a);
+        dft_tc_kernel<PCAL_DFT_TC_TF32X3><<<grid, kTcThreads, TcCfg<PCAL_DFT_TC_TF32X3>::kSmem, s>>>(a);
     else
-        dft_tc_kernel<PCAL_DFT_TC_BF16X3><<<grid, kTcThreads, kSmemTiles, s>>>(a);
+        dft_tc_kernel<PCAL_DFT_TC_BF16X3><<<grid, kTcThreads, TcCfg<PCAL_DFT_TC_BF16X3>::kSmem, s>>>(a);
     return cudaGetLastError();
 }
 

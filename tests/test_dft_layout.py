@@ -13,6 +13,7 @@ import pytest
 import paper_2501_05993_gb300 as pcal
 
 ESIZE = {"tf32x3": 4, "bf16x3": 2}
+TILE = {"tf32x3": 128, "bf16x3": 256}  # output columns per tile
 
 
 @pytest.fixture(scope="module")
@@ -55,15 +56,16 @@ def test_weight_tiles_decode_to_the_dft_matrix(lib, mode, N):
     es = ESIZE[mode]
     kcv = 128 // es
     n_cols = (2 * N + 15) // 16 * 16
-    tiles = (n_cols + 127) // 128
+    NT = TILE[mode]
+    tiles = (n_cols + NT - 1) // NT
     chunks = (2 * N + kcv - 1) // kcv
     tol = 2.0 ** -21 if mode == "tf32x3" else 2.0 ** -16
     for t in sorted({0, tiles - 1}):
         for c in sorted({0, chunks // 2, chunks - 1}):
             hi, lo, rows = pcal.pcal_dft_weights_host(N, mode, t, c)
-            assert rows == min(128, n_cols - 128 * t) and rows % 16 == 0
+            assert rows == min(NT, n_cols - NT * t) and rows % 16 == 0
             h, l = decode(hi, rows, es), decode(lo, rows, es)
-            n = 128 * t + np.arange(rows)[:, None]
+            n = NT * t + np.arange(rows)[:, None]
             k = c * kcv + np.arange(kcv)[None, :]
             w = expected(N, n, k)
             assert np.max(np.abs(h + l - w)) <= tol, (t, c)
@@ -77,7 +79,7 @@ def test_weight_tiles_decode_to_the_dft_matrix(lib, mode, N):
 
 def test_weights_reject_bad_arguments(lib):
     for args in [(0, "tf32x3", 0, 0), (1025, "tf32x3", 0, 0), (64, "tf32x3", 1, 0), (64, "bf16x3", 0, 2),
-                 (200, "tf32x3", 4, 0),
+                 (200, "tf32x3", 4, 0), (200, "bf16x3", 2, 0),
                  (64, "fp32", 0, 0)]:  # the CUDA-core mode has no weight tiles
         with pytest.raises(pcal.PcalError):
             pcal.pcal_dft_weights_host(*args)
