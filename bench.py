@@ -197,6 +197,37 @@ def cpu_oracle_rate(sample_samples: int):
     return sample_samples / dt / 1e9, dt
 
 
+def _direct_slice(job):
+    """One worker of the all-core direct oracle: the FP64 tone sums of its slice (phases referenced to the
+    slice's absolute start, so the slices' phasors add)."""
+    import oracle
+    import synth
+
+    n0, count = job
+    s = synth.Stream(fs=FS, fc=FC, fo=FO, amp=AMP, td=TD, seed=SEED)
+    host = s.bits2(n0, count)
+    t0 = time.perf_counter()
+    T = oracle.direct(host, "2bit", n0, FS, FC, FO)
+    return T, time.perf_counter() - t0
+
+
+def cpu_oracle_allcore_rate(sample: int):
+    """The oracle's direct definition on every core: one spawned process per core sums its own slice of the
+    bounded prefix, the phasors add.  Returns (Gsamples/s, cores, seconds)."""
+    import multiprocessing as mp
+
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    per = sample // cores // 64 * 64
+    jobs = [(k * per, per) for k in range(cores)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_direct_slice, [(0, 64)] * cores)  # workers import and warm up
+        parts = pool.map(_direct_slice, jobs)
+    t0 = time.perf_counter()
+    sum(T for T, _ in parts)
+    dt = max(d for _, d in parts) + (time.perf_counter() - t0)
+    return per * cores / dt / 1e9, cores, dt
+
+
 def _fold_counts_slice(job):
     """One worker of the all-core CPU fold: exact per-code counts of its slice."""
     import oracle
@@ -402,6 +433,14 @@ def run_gpu(args):
         v, dt = cpu_oracle_rate(args.cpu_sample)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"direct FP64 definition over the first {args.cpu_sample} samples ({dt:.1f} s)"}
+        try:
+            va, ca, dta = cpu_oracle_allcore_rate(4 * args.cpu_sample)
+            cpu.update({"value_allcore": va, "cores_allcore": ca,
+                        "sample_allcore": f"the same definition over the first {4 * args.cpu_sample} samples, one "
+                                          f"spawned process per core summing its slice ({dta:.1f} s, slowest slice "
+                                          f"+ the sum)"})
+        except Exception as e:
+            cpu["allcore_error"] = f"{type(e).__name__}: {e}"[:200]
         try:
             one, alln, cores = cpu_fold_rates(M)
             cpu_fold = {"value_1core": one, "value_allcore": alln, "unit": UNIT, "cores": cores, "kind": "oracle fold",
