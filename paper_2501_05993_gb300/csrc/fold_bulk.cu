@@ -659,12 +659,12 @@ int bulk_tiling(const pcal_plan* p, int64_t n_rows, BulkTiling* t) {
     const int64_t avg = (total + gr - 1) / gr;
     int64_t maxb = 2 * avg;
     if (maxb > cap) maxb = cap;
-    const int64_t stat = avg / 2;
+    const int64_t stat = avg * 3 / 4;
     z.row_groups = gr;
     z.total_boxes = (int)total;
     z.static_boxes = (int)stat;
     z.max_boxes = (int)maxb;
-    z.chunk = 4;  // boxes per grab (C2: 2 -> 4 and a static half instead of 3/4: -0.3 us per step)
+    z.chunk = 4;  // boxes per grab (2 -> 4: C2 -0.2 us per step, 1 GiB int8 launches 181 -> 164 us)
     z.rows_per_cta = maxb * box;  // the most rows one CTA can fold
     z.upper_planes = 0;
     if (p->g.format == PCAL_2BIT) {
