@@ -11,19 +11,23 @@
 // and three products hi.hi + hi.lo + lo.hi accumulate in FP32 in tensor
 // memory.  The tensor cores' FP32 accumulation loses about one unit in the
 // last place per MMA, in the same direction, so the error grows with the
-// number of MMAs an accumulator takes: the hi.hi products go to two
-// accumulators (even and odd K chunks) and the small cross products to a
-// third, and the three are added in FP32 at the end (error figures: pcal.h).
+// number of MMAs an accumulator takes: the hi.hi products and the small cross
+// products go to separate accumulators (split TF32, with twice the MMAs per K,
+// also splits hi.hi over even and odd K chunks), added in FP32 at the end
+// (error figures: pcal.h).
 //
-// Tiles.  A CTA owns 128 channels (MMA M, rows in TMEM lanes) x up to 256
-// (split BF16) or 128 (split TF32) output columns (MMA N) and walks
-// K = 2N in chunks of 128 bytes per row (32 TF32 or 64 BF16 values).  Per
-// chunk it converts its rows of P into the hi/lo A tiles in shared memory
-// while one 1-D bulk copy brings the chunk's precomputed hi/lo W tiles, then
-// one thread issues 4 K-steps x 3 products and commits them to an mbarrier.  Shared-memory tiles use the
-// no-swizzle K-major layout: 8-row x 16-byte core matrices, the core matrices
-// of one 8-row band along K `rows/8 * 128` bytes apart (leading byte offset)
-// and consecutive bands 128 bytes apart (stride byte offset).
+// Kernels.  split_p_kernel writes P as split operand tiles in the shared-
+// memory image layout.  dft_tc_kernel: a CTA owns 128 channels (MMA M, rows
+// in TMEM lanes) x up to 256 (split BF16) or 128 (split TF32) output columns
+// (MMA N) and walks K = 2N in chunks of 128 bytes per row (64 BF16 or 32 TF32
+// values); a producer thread streams each chunk's operand and weight tiles
+// into shared-memory stages with 1-D bulk copies, an MMA thread issues 4
+// K-steps x 3 products per chunk and commits them to the stage's empty
+// barrier, and the epilogue parks the accumulators in shared memory and
+// writes complex T row by row.  Shared-memory tiles use the no-swizzle
+// K-major layout: 8-row x 16-byte core matrices, the core matrices of one
+// 8-row band along K `rows/8 * 128` bytes apart (leading byte offset) and
+// consecutive bands 128 bytes apart (stride byte offset).
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
