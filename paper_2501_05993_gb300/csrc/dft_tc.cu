@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(256) split_p_kernel(const float2* __restrict__
 }
 
 
-// One CTA: 128 channels x up to 128 output columns.  Thread 0 streams the A
+// One CTA: 128 channels x up to TcCfg::kNT output columns.  Thread 0 streams the A
 // and B tile pairs of each chunk through kStages shared-memory stages (bulk
 // copies, full barriers); thread 32 issues the chunk's 4 K-steps x 3 products
 // and commits them to the stage's empty barrier, so a stage is refilled as
