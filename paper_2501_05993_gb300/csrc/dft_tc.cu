@@ -105,20 +105,29 @@ __host__ __device__ inline float f32_of_bits(uint32_t u) {
 #endif
 }
 
-// Split x into two parts of the MMA type, written at `hi` and `lo` (aligned
-// to the element size).
+// Split x into two parts of the MMA type (bit patterns in the low bits).
+template <int MODE>
+__host__ __device__ inline void split_parts(float x, uint32_t& h, uint32_t& l) {
+    if (MODE == PCAL_DFT_TC_TF32X3) {
+        h = tf32_bits_rna(x);
+        l = tf32_bits_rna(x - f32_of_bits(h));
+    } else {
+        h = bf16_bits_rn(x);
+        l = bf16_bits_rn(x - f32_of_bits(h << 16));
+    }
+}
+
+// Split x, written at `hi` and `lo` (aligned to the element size).
 template <int MODE>
 __host__ __device__ inline void split_store(float x, uint8_t* hi, uint8_t* lo) {
+    uint32_t h, l;
+    split_parts<MODE>(x, h, l);
     if (MODE == PCAL_DFT_TC_TF32X3) {
-        const uint32_t h = tf32_bits_rna(x);
-        const uint32_t l = tf32_bits_rna(x - f32_of_bits(h));
         *reinterpret_cast<uint32_t*>(hi) = h;
         *reinterpret_cast<uint32_t*>(lo) = l;
     } else {
-        const uint16_t h = bf16_bits_rn(x);
-        const uint16_t l = bf16_bits_rn(x - f32_of_bits((uint32_t)h << 16));
-        *reinterpret_cast<uint16_t*>(hi) = h;
-        *reinterpret_cast<uint16_t*>(lo) = l;
+        *reinterpret_cast<uint16_t*>(hi) = (uint16_t)h;
+        *reinterpret_cast<uint16_t*>(lo) = (uint16_t)l;
     }
 }
 
@@ -226,35 +235,73 @@ struct DftTcArgs {
 
 // P -> split operand tiles: row tile mt, chunk kc holds rows 128 mt.. and K
 // values kc*KC.. of [Re P | Im P] (zeros past C and 2N) as hi and lo tile
-// images.  One block per tile: the threads read P along K (consecutive
-// threads, consecutive values of a row), build the two images in shared
-// memory, then store them as contiguous 16-byte words.
+// images.  With 128 rows, 16-byte word w = g*128 + r of an image is row r's
+// K values g*V .. g*V+V-1 of the chunk (V = 16 / element size: one core-
+// matrix row), so a thread per word reads V consecutive values of one row of
+// P (whole sectors) and consecutive threads store consecutive words.
+constexpr int kImageWords = kATile / 16;  // 16-byte words of one tile image
+
 template <int MODE>
-__global__ void __launch_bounds__(256) split_p_kernel(const float2* __restrict__ P, int64_t C, int N, int k_chunks,
-                                                      uint8_t* __restrict__ out, int64_t tiles) {
+__host__ __device__ inline void split_word(const float2* __restrict__ P, int64_t C, int N, int k_chunks,
+                                           int64_t blk, int w, uint4& hi, uint4& lo) {
     constexpr int ES = esize_of<MODE>();
     constexpr int KC = kChunkBytes / ES;
-    __shared__ __align__(16) uint8_t img[2 * kATile];
-    for (int64_t blk = blockIdx.x; blk < tiles; blk += gridDim.x) {
-        const int kc = (int)(blk % k_chunks);
-        const int64_t m0 = (blk / k_chunks) * kTcM;
-        for (int e = threadIdx.x; e < kTcM * KC; e += blockDim.x) {
-            const int r = e / KC, k = e % KC;
-            const int64_t c = m0 + r;
-            const int kk = kc * KC + k;
-            float x = 0.f;
-            if (c < C && kk < 2 * N) {
-                const float2 pv = P[c * N + (kk < N ? kk : kk - N)];
-                x = kk < N ? pv.x : pv.y;
+    constexpr int V = 16 / ES;
+    const int r = w % kTcM, g = w / kTcM;
+    const int64_t c = (blk / k_chunks) * kTcM + r;
+    const int kk0 = (int)(blk % k_chunks) * KC + g * V;
+    float x[V];
+    for (int j = 0; j < V; ++j) x[j] = 0.f;
+    if (c < C) {
+        const bool im = kk0 >= N;
+        const int64_t src = c * N + (im ? kk0 - N : kk0);
+        const bool whole = kk0 + V <= (im ? 2 * N : N);
+        if (whole && (reinterpret_cast<uintptr_t>(P + src) & 15) == 0) {
+            const float4* q = reinterpret_cast<const float4*>(P + src);
+#pragma unroll
+            for (int j = 0; j < V / 2; ++j) {
+                const float4 v = q[j];
+                x[2 * j] = im ? v.y : v.x;
+                x[2 * j + 1] = im ? v.w : v.z;
             }
-            const uint32_t o = tile_offset(r, k, kTcM, ES);
-            split_store<MODE>(x, img + o, img + kATile + o);
+        } else {
+            for (int j = 0; j < V; ++j) {
+                const int kk = kk0 + j;
+                if (kk < N)
+                    x[j] = P[c * N + kk].x;
+                else if (kk < 2 * N)
+                    x[j] = P[c * N + kk - N].y;
+            }
         }
-        __syncthreads();
-        uint4* dst = reinterpret_cast<uint4*>(out + (size_t)blk * 2 * kATile);
-        const uint4* src = reinterpret_cast<const uint4*>(img);
-        for (int i = threadIdx.x; i < 2 * kATile / 16; i += blockDim.x) dst[i] = src[i];
-        __syncthreads();
+    }
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if constexpr (MODE == PCAL_DFT_TC_TF32X3) {
+            split_parts<MODE>(x[i], h[i], l[i]);
+        } else {
+            uint32_t h0, l0, h1, l1;
+            split_parts<MODE>(x[2 * i], h0, l0);
+            split_parts<MODE>(x[2 * i + 1], h1, l1);
+            h[i] = h0 | h1 << 16;
+            l[i] = l0 | l1 << 16;
+        }
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) split_p_kernel(const float2* __restrict__ P, int64_t C, int N, int k_chunks,
+                                                      uint4* __restrict__ out, int64_t words) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += stride) {
+        const int64_t blk = i / kImageWords;
+        const int w = (int)(i % kImageWords);
+        uint4 hi, lo;
+        split_word<MODE>(P, C, N, k_chunks, blk, w, hi, lo);
+        out[blk * 2 * kImageWords + w] = hi;
+        out[blk * 2 * kImageWords + kImageWords + w] = lo;
     }
 }
 
@@ -589,12 +636,14 @@ cudaError_t launch_dft(pcal_dft* d, const float2* P, int64_t C, float2* T, cudaS
     }
     const int64_t m_tiles = (C + kTcM - 1) / kTcM;
     if ((size_t)m_tiles * d->k_chunks * 2 * kATile > d->a_cap) return cudaErrorInvalidValue;  // dft_reserve first
-    const int64_t total = m_tiles * d->k_chunks;  // tiles
-    const int sgrid = (int)(total < 8 * 152 ? total : 8 * 152);
+    const int64_t words = m_tiles * d->k_chunks * kImageWords;  // one thread per word (hi and lo)
+    const int64_t blocks = (words + 255) / 256;
+    const int sgrid = (int)(blocks < 32 * 152 ? blocks : 32 * 152);
+    uint4* a_words = reinterpret_cast<uint4*>(d->d_a);
     if (d->mode == PCAL_DFT_TC_TF32X3)
-        split_p_kernel<PCAL_DFT_TC_TF32X3><<<sgrid, 256, 0, s>>>(P, C, d->N, d->k_chunks, d->d_a, total);
+        split_p_kernel<PCAL_DFT_TC_TF32X3><<<sgrid, 256, 0, s>>>(P, C, d->N, d->k_chunks, a_words, words);
     else
-        split_p_kernel<PCAL_DFT_TC_BF16X3><<<sgrid, 256, 0, s>>>(P, C, d->N, d->k_chunks, d->d_a, total);
+        split_p_kernel<PCAL_DFT_TC_BF16X3><<<sgrid, 256, 0, s>>>(P, C, d->N, d->k_chunks, a_words, words);
     DftTcArgs a{};
     a.T = T;
     a.a = d->d_a;
