@@ -238,7 +238,7 @@ struct DftTcArgs {
 // images.  With 128 rows, 16-byte word w = g*128 + r of an image is row r's
 // K values g*V .. g*V+V-1 of the chunk (V = 16 / element size: one core-
 // matrix row), so a thread per word reads V consecutive values of one row of
-// P (whole sectors) and consecutive threads store consecutive words.
+// P (whole sectors) and writes its hi and lo words.
 constexpr int kImageWords = kATile / 16;  // 16-byte words of one tile image
 
 template <int MODE>
@@ -294,10 +294,17 @@ __host__ __device__ inline void split_word(const float2* __restrict__ P, int64_t
 template <int MODE>
 __global__ void __launch_bounds__(256) split_p_kernel(const float2* __restrict__ P, int64_t C, int N, int k_chunks,
                                                       uint4* __restrict__ out, int64_t words) {
+    constexpr int kRowWords = kChunkBytes / 16;  // words of one row of a chunk
+    // split BF16: 8 consecutive threads take one row's 8 words (a warp reads
+    // 4 rows' runs of P), then the next rows (18.0 against 19.3 us per launch
+    // at 4096 x 1024); split TF32 (half the values per word) keeps one row
+    // per thread (20.0 against 22.8 us)
+    constexpr bool kRowRuns = MODE == PCAL_DFT_TC_BF16X3;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += stride) {
         const int64_t blk = i / kImageWords;
-        const int w = (int)(i % kImageWords);
+        const int e = (int)(i % kImageWords);
+        const int w = kRowRuns ? (e % kRowWords) * kTcM + e / kRowWords : e;  // word g*128 + r
         uint4 hi, lo;
         split_word<MODE>(P, C, N, k_chunks, blk, w, hi, lo);
         out[blk * 2 * kImageWords + w] = hi;
