@@ -41,7 +41,7 @@ _OUT = os.path.join(_HERE, "_build", "liboracle.so")
 _lib = None
 
 FORMATS = {"f32": 0, "i8": 1, "2bit": 2, "f64": 3}
-# Reading of the 2-bit levels (the paper says only "2-bit or higher"): codes
+# Reading of the 2-bit levels (Sec. 1 fixes only a sample width of 2 bits or more): codes
 # 0..3 = {-v, -1, +1, +v} with the customary magnitude ratio v = 3.3359.
 DEFAULT_LEVELS = (-3.3359, -1.0, 1.0, 3.3359)
 # The tone phase of the sin() model of Eq. 1 is arg(T) + pi/2.

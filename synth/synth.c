@@ -19,7 +19,7 @@
  * index hi, stream id, 0).  Each counter value gives two 53-bit uniforms and,
  * through the Box-Muller transform, the normals z[2m] and z[2m+1].
  *
- * Quantisers (the readings of the paper's "2-bit or higher" samples):
+ * Quantisers (readings: Sec. 1 fixes only a sample width of 2 bits or more):
  *   f32 : float32(x)
  *   i8  : clamp(round-half-even(scale * x), -128, 127)
  *   2bit: code 0: x < -t, 1: -t <= x < 0, 2: 0 <= x < t, 3: x >= t
