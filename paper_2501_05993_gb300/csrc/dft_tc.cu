@@ -291,20 +291,24 @@ __host__ __device__ inline void split_word(const float2* __restrict__ P, int64_t
     lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
+// Word (g*128 + r) of a tile image that thread e of the tile writes.  Split
+// BF16: 8 consecutive threads take one row's 8 words (a warp reads 4 rows'
+// runs of P), then the next rows (18.0 against 19.3 us per launch at
+// 4096 x 1024); split TF32 (half the values per word) keeps one row per
+// thread (20.0 against 22.8 us).
+template <int MODE>
+__host__ __device__ inline int split_word_of_thread(int e) {
+    constexpr int kRowWords = kChunkBytes / 16;  // words of one row of a chunk
+    return MODE == PCAL_DFT_TC_BF16X3 ? (e % kRowWords) * kTcM + e / kRowWords : e;
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(256) split_p_kernel(const float2* __restrict__ P, int64_t C, int N, int k_chunks,
                                                       uint4* __restrict__ out, int64_t words) {
-    constexpr int kRowWords = kChunkBytes / 16;  // words of one row of a chunk
-    // split BF16: 8 consecutive threads take one row's 8 words (a warp reads
-    // 4 rows' runs of P), then the next rows (18.0 against 19.3 us per launch
-    // at 4096 x 1024); split TF32 (half the values per word) keeps one row
-    // per thread (20.0 against 22.8 us)
-    constexpr bool kRowRuns = MODE == PCAL_DFT_TC_BF16X3;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += stride) {
         const int64_t blk = i / kImageWords;
-        const int e = (int)(i % kImageWords);
-        const int w = kRowRuns ? (e % kRowWords) * kTcM + e / kRowWords : e;  // word g*128 + r
+        const int w = split_word_of_thread<MODE>((int)(i % kImageWords));
         uint4 hi, lo;
         split_word<MODE>(P, C, N, k_chunks, blk, w, hi, lo);
         out[blk * 2 * kImageWords + w] = hi;

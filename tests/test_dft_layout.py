@@ -7,6 +7,10 @@ each value split in two parts of the MMA type.  Decoding a tile with the no-swiz
 bands 128 bytes apart) must give back the matrix entries to the precision of the
 split, and zeros in the padding.
 """
+import os
+import shutil
+import subprocess
+
 import numpy as np
 import pytest
 
@@ -83,3 +87,21 @@ def test_weights_reject_bad_arguments(lib):
                  (64, "fp32", 0, 0)]:  # the CUDA-core mode has no weight tiles
         with pytest.raises(pcal.PcalError):
             pcal.pcal_dft_weights_host(*args)
+
+
+def test_operand_split_matches_the_tile_layout(tmp_path):
+    """The split kernel's per-thread words (its loop body run on the host)
+    equal the element-wise split of [Re P | Im P] into the tile layout, for
+    ragged C and N and 8-byte-aligned P, and each mode's thread -> word map is
+    a bijection on a tile (tests/host/dft_split_check.cu)."""
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not found")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    exe = tmp_path / "dft_split_check"
+    subprocess.check_call([nvcc, "-std=c++17", "-O2", "-gencode", "arch=compute_103a,code=sm_103a",
+                           "-I", os.path.join(root, "paper_2501_05993_gb300", "csrc"), "-I", os.path.join(root, "include"),
+                           os.path.join(root, "tests", "host", "dft_split_check.cu"), "-o", str(exe)])
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert r.stdout.strip().endswith("OK")
