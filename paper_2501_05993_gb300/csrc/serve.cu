@@ -30,6 +30,7 @@
 #include <thread>
 #include <vector>
 
+#include "arena.h"
 #include "internal.cuh"
 
 namespace {
@@ -42,51 +43,7 @@ double now_s() {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-// First-fit allocator over one device allocation (host-side bookkeeping).
-class Arena {
-  public:
-    void reset(size_t size) {
-        free_.clear();
-        if (size) free_[0] = size;
-        used_ = 0;
-    }
-    bool alloc(size_t bytes, size_t* off) {
-        bytes = align_up(bytes, 256);
-        for (auto it = free_.begin(); it != free_.end(); ++it) {
-            if (it->second < bytes) continue;
-            *off = it->first;
-            const size_t rest = it->second - bytes;
-            const size_t at = it->first + bytes;
-            free_.erase(it);
-            if (rest) free_[at] = rest;
-            used_ += bytes;
-            return true;
-        }
-        return false;
-    }
-    void release(size_t off, size_t bytes) {
-        bytes = align_up(bytes, 256);
-        used_ -= bytes;
-        auto it = free_.emplace(off, bytes).first;
-        auto next = std::next(it);
-        if (next != free_.end() && it->first + it->second == next->first) {
-            it->second += next->second;
-            free_.erase(next);
-        }
-        if (it != free_.begin()) {
-            auto prev = std::prev(it);
-            if (prev->first + prev->second == it->first) {
-                prev->second += it->second;
-                free_.erase(it);
-            }
-        }
-    }
-    size_t used() const { return used_; }
-
-  private:
-    std::map<size_t, size_t> free_;
-    size_t used_ = 0;
-};
+using pcal_arena::Arena;
 
 enum StreamState { kQueued, kActive, kClosing, kReleased };
 

@@ -149,6 +149,18 @@ def test_bulk_tiling_invariants(lib, fs, fc, fo, fmt, num_sms, n_rows):
     assert t.smem_bytes + 1024 <= 227 * 1024
 
 
+def test_server_arena_on_host(tmp_path):
+    """The serving runtime's HBM arena (first fit, coalescing free blocks)
+    against a brute-force per-unit model on random alloc / release sequences."""
+    exe = tmp_path / "arena_check"
+    src = os.path.join(ROOT, "tests", "host", "arena_check.cpp")
+    inc = os.path.join(ROOT, "paper_2501_05993_gb300", "csrc")
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-I", inc, src, "-o", str(exe)])
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert r.stdout.strip().endswith("OK")
+
+
 def test_double_float_arithmetic_on_host(tmp_path):
     exe = tmp_path / "df64_check"
     src = os.path.join(ROOT, "tests", "host", "df64_check.cpp")
