@@ -237,6 +237,8 @@ typedef struct {
     int64_t bytes_folded;   /* sample bytes folded on the device            */
 } pcal_stats;
 
+/* Copy the plan's counters into *out (host bookkeeping; no CUDA call, no
+ * synchronisation).  PCAL_EINVAL for a NULL argument. */
 int pcal_get_stats(const pcal_plan* plan, pcal_stats* out);
 
 /*
@@ -253,6 +255,9 @@ typedef struct {
     int32_t total_boxes, static_boxes, max_boxes;  /* per column group; per CTA */
 } pcal_tiling;
 
+/* fs, f_comb, f_offset, N, sample_format: as pcal_plan_create; num_sms >= 1;
+ * n_rows >= 1 rows of the plan's row_samples (pcal_plan_geometry); *out is
+ * written on PCAL_OK. */
 int pcal_bulk_tiling(double fs, double f_comb, double f_offset, int N, int sample_format, int num_sms,
                      int64_t n_rows, pcal_tiling* out);
 
@@ -380,6 +385,9 @@ int pcal_batch_result_device(const pcal_batch* batch, int channel, const double*
  * int64 [L][4] per-code counts; int8: int64 [L] sums. */
 int pcal_batch_get_bins(pcal_batch* batch, int channel, int64_t* host_out);
 
+/* The batch's counters summed over its channels (n_abs: samples accumulated;
+ * n_period is not kept and stays 0): host bookkeeping, no synchronisation.
+ * PCAL_EINVAL for a NULL argument. */
 int pcal_batch_get_stats(const pcal_batch* batch, pcal_stats* out);
 
 /*
@@ -481,8 +489,13 @@ int pcal_server_get_stats(pcal_server* server, pcal_server_stats* out);
 
 typedef struct pcal_rotfold pcal_rotfold;
 
+/* fs, f_comb, f_offset, N: as pcal_plan_create (the same geometry checks);
+ * sample_format PCAL_I8 or PCAL_F32; variant one of PCAL_ROT_*; lanes
+ * 1..4096 accumulators per bin.  Allocates the device state, which the
+ * object owns (PCAL_ENOMEM, PCAL_ECUDA); PCAL_EINVAL for other values. */
 int pcal_rotfold_create(double fs, double f_comb, double f_offset, int N, int sample_format, int variant, int lanes,
                         pcal_rotfold** out);
+/* Frees the object's device state once its work has finished (NULL: no-op). */
 int pcal_rotfold_destroy(pcal_rotfold* r);
 /* samples: DEVICE, n samples continuing the absolute index; asynchronous on stream. */
 int pcal_rotfold_accumulate(pcal_rotfold* r, const void* samples, int64_t n, void* stream);
@@ -508,8 +521,14 @@ int pcal_rotfold_get_acc(pcal_rotfold* r, float* host_out);
  */
 typedef struct pcal_rotplan pcal_rotplan;
 
+/* fs, f_comb: integral Hz with N = fs/f_comb (PCAL_EINVAL otherwise),
+ * N <= PCAL_BATCH_MAX_N (PCAL_ETOOLARGE); 0 <= f_offset < f_comb, any value;
+ * sample_format PCAL_F32, PCAL_I8 or PCAL_2BIT.  Allocates the device state,
+ * which the object owns (PCAL_ENOMEM, PCAL_ECUDA). */
 int pcal_rotplan_create(double fs, double f_comb, double f_offset, int N, int sample_format, pcal_rotplan** out);
+/* Waits for the object's last stream, then frees it (NULL: no-op). */
 int pcal_rotplan_destroy(pcal_rotplan* plan);
+/* 2-bit decode levels of codes 0..3 (host array, copied), as pcal_plan_set_levels. */
 int pcal_rotplan_set_levels(pcal_rotplan* plan, const double levels[4]);
 /* samples: DEVICE, n samples continuing the absolute index; asynchronous on stream. */
 int pcal_rotplan_accumulate(pcal_rotplan* plan, const void* samples, int64_t n, void* stream);
@@ -550,10 +569,17 @@ int pcal_rotplan_read_results(pcal_rotplan* plan, double* phasors, double* amp, 
 #define PCAL_DFT_TC_BF16X3 2
 typedef struct pcal_dft pcal_dft;
 
+/* PCAL_EINVAL for N or mode out of range, PCAL_ENOMEM / PCAL_ECUDA when the
+ * device state cannot be made; the object owns it. */
 int pcal_dft_create(int N, int mode, pcal_dft** out);
+/* Synchronises the device and frees the object (NULL: no-op). */
 int pcal_dft_destroy(pcal_dft* dft);
+/* PCAL_EINVAL for C < 0 or NULL P / T with C > 0; PCAL_ETOOLARGE beyond C
+ * limit; C = 0 launches nothing. */
 int pcal_dft_execute(pcal_dft* dft, const void* P, int64_t C, void* T, void* stream);
 int pcal_dft_check(pcal_dft* dft, unsigned int* flags_out);
+/* PCAL_EINVAL for the CUDA-core mode, N out of range, or tile / chunk
+ * outside the weight matrix. */
 int pcal_dft_weights_host(int N, int mode, int tile, int chunk, void* hi, void* lo, int* rows);
 
 /*
