@@ -164,9 +164,18 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
+        text = open(self.path).read()
+        os.unlink(self.path)
+        return self.parse(text)
+
+    @staticmethod
+    def parse(text: str) -> dict:
+        """Median SM clock, highest max clock and the throttle reasons seen
+        active, from nvidia-smi's csv rows in FIELDS order (malformed rows
+        skipped)."""
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path).read().splitlines():
+        for line in text.splitlines():
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -178,7 +187,6 @@ class ClockSampler:
             for name, v in zip(names, parts[5:9]):
                 if v.lower() == "active":
                     reasons.add(name)
-        os.unlink(self.path)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
 
