@@ -41,3 +41,21 @@ def test_traffic_only_while_the_source_matches(tmp_path, monkeypatch):
     with open(csrc / "fold_bulk.cu", "a") as f:
         f.write("\n// changed\n")
     assert bench.read_traffic("fold_bulk.cu") is None
+
+
+def test_clock_sampler_stop_reads_and_removes_its_file(tmp_path):
+    class FakeProc:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    path = tmp_path / "clocks.csv"
+    path.write_text(ROW.format(sm=2070, mask="0", hw="Not Active", hwt="Not Active", swt="Not Active",
+                               pcap="Not Active") + "\n")
+    s = bench.ClockSampler(0)
+    s.proc, s.path = FakeProc(), str(path)
+    r = s.stop()
+    assert r["sm_mhz"] == 2070 and r["reasons"] == [] and r["samples"] == 1
+    assert not path.exists()
