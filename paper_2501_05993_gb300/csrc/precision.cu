@@ -22,6 +22,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <new>
+
 #include "internal.cuh"
 
 namespace {
@@ -175,7 +177,8 @@ extern "C" int pcal_rotfold_create(double fs, double f_comb, double f_offset, in
     if ((sample_format != PCAL_I8 && sample_format != PCAL_F32) || variant < PCAL_ROT_TABLE ||
         variant > PCAL_ROT_DFR || lanes < 1 || lanes > 4096)
         return PCAL_EINVAL;
-    pcal_rotfold* r = new pcal_rotfold();
+    pcal_rotfold* r = new (std::nothrow) pcal_rotfold();
+    if (!r) return PCAL_ENOMEM;
     r->fs = g.fs;
     r->fc = g.f_comb;
     r->fo = g.f_offset;

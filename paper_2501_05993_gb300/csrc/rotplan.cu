@@ -14,6 +14,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <new>
+
 #include "df64.cuh"
 #include "internal.cuh"
 
@@ -133,7 +135,8 @@ extern "C" int pcal_rotplan_create(double fs, double f_comb, double f_offset, in
         (void)cudaGetLastError();
         return PCAL_ECUDA;
     }
-    pcal_rotplan* r = new pcal_rotplan();
+    pcal_rotplan* r = new (std::nothrow) pcal_rotplan();
+    if (!r) return PCAL_ENOMEM;
     r->fs = ifs;
     r->fc = ifc;
     r->fo = f_offset;

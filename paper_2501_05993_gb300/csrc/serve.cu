@@ -27,6 +27,7 @@
 #include <deque>
 #include <map>
 #include <mutex>
+#include <new>
 #include <thread>
 #include <vector>
 
@@ -396,7 +397,8 @@ extern "C" int pcal_server_create(const pcal_server_config* cfg, pcal_server** o
     if (!cfg || cfg->hbm_budget_bytes <= 0 || cfg->max_streams <= 0 || cfg->max_streams > PCAL_MAX_BATCH ||
         !(cfg->period_s > 0.0) || !(cfg->ring_s > 0.0))
         return PCAL_EINVAL;
-    pcal_server* s = new pcal_server();
+    pcal_server* s = new (std::nothrow) pcal_server();
+    if (!s) return PCAL_ENOMEM;
     s->cfg = *cfg;
     s->sched = pcal_schedule{0, 32, 0, 90, 4, 224};
     s->slot_owner.assign(cfg->max_streams, -1);
