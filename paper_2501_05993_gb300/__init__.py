@@ -236,6 +236,30 @@ def pcal_plan_set_levels(plan: int, levels) -> None:
     _check(load().pcal_plan_set_levels(plan, lv), "pcal_plan_set_levels")
 
 
+def device_sample_count(samples, fmt: str, n: int | None) -> int:
+    """Samples to fold from `samples`: n, or all a tensor holds.  A tensor must
+    be a contiguous CUDA tensor with elements of the format's size (1 byte for
+    "2bit" and "i8", 4 for "f32"), and n may not exceed what it holds; an
+    integer address needs an explicit n.  Raises ValueError otherwise."""
+    if not hasattr(samples, "data_ptr"):
+        if n is None:
+            raise ValueError("an address needs an explicit sample count n")
+        return int(n)
+    if not samples.is_cuda:
+        raise ValueError("samples must be a CUDA tensor (host arrays go through accumulate_host)")
+    if not samples.is_contiguous():
+        raise ValueError("samples must be contiguous")
+    esize = 4 if fmt == "f32" else 1
+    if samples.element_size() != esize:
+        raise ValueError(f"{fmt} samples are {esize}-byte elements, got {samples.element_size()}-byte ones")
+    held = samples.numel() * (4 if fmt == "2bit" else 1)
+    if n is None:
+        return held
+    if int(n) > held:
+        raise ValueError(f"n = {int(n)} exceeds the {held} samples the tensor holds")
+    return int(n)
+
+
 def pcal_accumulate(plan: int, samples, n: int, stream=None) -> None:
     _check(load().pcal_accumulate(plan, _ptr(samples), int(n), _stream(stream)), "pcal_accumulate")
 
@@ -387,9 +411,7 @@ class Plan:
     def accumulate(self, samples, n: int | None = None, stream=None):
         """Fold device samples (a torch CUDA tensor of the plan's format, or
         an address with an explicit n)."""
-        if n is None:
-            n = samples.numel() * (4 if self.fmt == "2bit" else 1)
-        pcal_accumulate(self.handle, samples, n, stream)
+        pcal_accumulate(self.handle, samples, device_sample_count(samples, self.fmt, n), stream)
 
     def accumulate_host(self, host: np.ndarray, n: int | None = None, stream=None):
         if n is None:

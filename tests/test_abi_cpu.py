@@ -169,3 +169,43 @@ def test_double_float_arithmetic_on_host(tmp_path):
     r = subprocess.run([str(exe)], capture_output=True, text=True)
     assert r.returncode == 0, r.stdout + r.stderr
     assert r.stdout.strip().endswith("OK")
+
+
+class _FakeDeviceTensor:
+    """The attributes Plan.accumulate reads from a torch CUDA tensor."""
+
+    def __init__(self, numel, esize, cuda=True, contiguous=True):
+        self._numel, self._esize, self.is_cuda, self._contig = numel, esize, cuda, contiguous
+
+    def data_ptr(self):
+        return 4096
+
+    def numel(self):
+        return self._numel
+
+    def element_size(self):
+        return self._esize
+
+    def is_contiguous(self):
+        return self._contig
+
+
+def test_device_sample_count_checks_the_tensor():
+    count = pcal.device_sample_count
+    assert count(_FakeDeviceTensor(100, 1), "2bit", None) == 400
+    assert count(_FakeDeviceTensor(100, 1), "2bit", 396) == 396
+    assert count(_FakeDeviceTensor(100, 1), "i8", None) == 100
+    assert count(_FakeDeviceTensor(100, 4), "f32", None) == 100
+    assert count(12345, "f32", 7) == 7  # an address with an explicit count
+    bad = [(_FakeDeviceTensor(100, 1), "2bit", 404),           # more than the tensor holds
+           (_FakeDeviceTensor(100, 4), "i8", None),            # float32 data for an int8 plan
+           (_FakeDeviceTensor(100, 1), "f32", None),           # bytes for a float32 plan
+           (_FakeDeviceTensor(100, 1, contiguous=False), "i8", None),
+           (_FakeDeviceTensor(100, 1, cuda=False), "i8", None),  # host data
+           (12345, "i8", None)]                                  # an address without a count
+    for args in bad:
+        with pytest.raises(ValueError):
+            count(*args)
+    import torch
+    with pytest.raises(ValueError):
+        count(torch.zeros(16, dtype=torch.uint8), "2bit", None)  # a real CPU tensor
