@@ -583,13 +583,22 @@ class Batch:
     def __len__(self):
         return len(self.channels)
 
+    def _check_tensors(self, samples, n):
+        names = {v: k for k, v in FORMATS.items()}
+        for c, x in enumerate(samples):
+            if hasattr(x, "data_ptr") and c < len(self.channels):
+                fmt = self.channels[c][3]
+                device_sample_count(x, fmt if isinstance(fmt, str) else names[int(fmt)], n[c])
+
     def accumulate(self, samples, n, stream=None):
+        self._check_tensors(samples, n)
         pcal_batch_accumulate(self.handle, samples, n, stream)
 
     def finalize_device(self, stream=None):
         pcal_batch_finalize_device(self.handle, stream)
 
     def step_graph(self, samples, n, stream=None):
+        self._check_tensors(samples, n)
         pcal_batch_step_graph(self.handle, samples, n, stream)
 
     def results(self, channel: int) -> dict:
@@ -723,6 +732,7 @@ class RotFold:
         _check(load().pcal_rotfold_create(float(fs), float(f_comb), float(f_offset), self.N, FORMATS[fmt],
                                           ROT_VARIANTS[variant], self.lanes, ctypes.byref(h)), "pcal_rotfold_create")
         self.handle = h.value
+        self.fmt = fmt
 
     def close(self):
         if getattr(self, "handle", None):
@@ -742,7 +752,8 @@ class RotFold:
         self.close()
 
     def accumulate(self, samples, n: int, stream=None):
-        _check(load().pcal_rotfold_accumulate(self.handle, _ptr(samples), int(n), _stream(stream)),
+        n = device_sample_count(samples, self.fmt, n)
+        _check(load().pcal_rotfold_accumulate(self.handle, _ptr(samples), n, _stream(stream)),
                "pcal_rotfold_accumulate")
 
     def acc(self) -> np.ndarray:
@@ -768,6 +779,7 @@ class RotPlan:
         _check(load().pcal_rotplan_create(float(fs), float(f_comb), float(f_offset), self.N, FORMATS[fmt],
                                           ctypes.byref(h)), "pcal_rotplan_create")
         self.handle = h.value
+        self.fmt = fmt
 
     def close(self):
         if getattr(self, "handle", None):
@@ -787,7 +799,8 @@ class RotPlan:
         self.close()
 
     def accumulate(self, samples, n: int, stream=None):
-        _check(load().pcal_rotplan_accumulate(self.handle, _ptr(samples), int(n), _stream(stream)),
+        n = device_sample_count(samples, self.fmt, n)
+        _check(load().pcal_rotplan_accumulate(self.handle, _ptr(samples), n, _stream(stream)),
                "pcal_rotplan_accumulate")
 
     def finalize_device(self, stream=None):
@@ -842,6 +855,13 @@ class Dft:
         self.close()
 
     def execute(self, P, C: int, T, stream=None):
+        """T[:C] = the tone DFT of P[:C] (C x N complex64, CUDA tensors or addresses)."""
+        for name, x in (("P", P), ("T", T)):
+            if hasattr(x, "data_ptr"):
+                if not x.is_cuda or not x.is_contiguous() or x.element_size() != 8:
+                    raise ValueError(f"{name} must be a contiguous complex64 CUDA tensor")
+                if x.numel() < int(C) * self.N:
+                    raise ValueError(f"{name} holds {x.numel()} values, fewer than C x N = {int(C) * self.N}")
         _check(load().pcal_dft_execute(self.handle, _ptr(P), int(C), _ptr(T), _stream(stream)), "pcal_dft_execute")
 
     def check(self) -> int:

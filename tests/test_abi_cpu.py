@@ -209,3 +209,24 @@ def test_device_sample_count_checks_the_tensor():
     import torch
     with pytest.raises(ValueError):
         count(torch.zeros(16, dtype=torch.uint8), "2bit", None)  # a real CPU tensor
+
+
+def test_dft_and_batch_wrappers_check_tensors():
+    """Dft.execute and Batch.accumulate refuse tensors they would misread,
+    before any library call (a stand-in object in place of a live handle)."""
+    import types
+
+    dft = types.SimpleNamespace(N=64, handle=None)
+    good = _FakeDeviceTensor(4 * 64, 8)
+    for P, T, C in [(_FakeDeviceTensor(4 * 64, 4), good, 4),          # float32, not complex64
+                    (good, _FakeDeviceTensor(4 * 64, 8, cuda=False), 4),
+                    (good, _FakeDeviceTensor(4 * 64, 8, contiguous=False), 4),
+                    (good, good, 5)]:                                # C x N beyond the tensors
+        with pytest.raises(ValueError):
+            pcal.Dft.execute(dft, P, C, T)
+    batch = types.SimpleNamespace(channels=[(64e6, 1e6, 1e4, "2bit"), (64e6, 1e6, 1e4, pcal.PCAL_I8)])
+    pcal.Batch._check_tensors(batch, [_FakeDeviceTensor(100, 1), 12345], [400, 7])   # fine
+    for samples, n in [([_FakeDeviceTensor(100, 1), 0], [404, 0]),                  # beyond the 2-bit tensor
+                       ([0, _FakeDeviceTensor(100, 4)], [0, 100])]:                  # float32 for an int8 channel
+        with pytest.raises(ValueError):
+            pcal.Batch._check_tensors(batch, samples, n)
