@@ -260,6 +260,24 @@ def device_sample_count(samples, fmt: str, n: int | None) -> int:
     return int(n)
 
 
+def host_sample_count(host: np.ndarray, fmt: str, n: int | None) -> int:
+    """Samples to take from a host array: n, or all it holds.  The array must
+    be C-contiguous with elements of the format's size (1 byte for "2bit" and
+    "i8", 4 for "f32"), and n may not exceed what it holds.  Raises ValueError
+    otherwise."""
+    if not host.flags.c_contiguous:
+        raise ValueError("host samples must be C-contiguous")
+    esize = 4 if fmt == "f32" else 1
+    if host.itemsize != esize:
+        raise ValueError(f"{fmt} samples are {esize}-byte elements, got {host.itemsize}-byte ones")
+    held = host.size * (4 if fmt == "2bit" else 1)
+    if n is None:
+        return held
+    if int(n) > held:
+        raise ValueError(f"n = {int(n)} exceeds the {held} samples the array holds")
+    return int(n)
+
+
 def pcal_accumulate(plan: int, samples, n: int, stream=None) -> None:
     _check(load().pcal_accumulate(plan, _ptr(samples), int(n), _stream(stream)), "pcal_accumulate")
 
@@ -414,14 +432,10 @@ class Plan:
         pcal_accumulate(self.handle, samples, device_sample_count(samples, self.fmt, n), stream)
 
     def accumulate_host(self, host: np.ndarray, n: int | None = None, stream=None):
-        if n is None:
-            n = host.size * (4 if self.fmt == "2bit" else 1)
-        pcal_accumulate_host(self.handle, host, n, stream)
+        pcal_accumulate_host(self.handle, host, host_sample_count(host, self.fmt, n), stream)
 
     def accumulate_host_async(self, host: np.ndarray, n: int | None = None, stream=None):
-        if n is None:
-            n = host.size * (4 if self.fmt == "2bit" else 1)
-        pcal_accumulate_host_async(self.handle, host, n, stream)
+        pcal_accumulate_host_async(self.handle, host, host_sample_count(host, self.fmt, n), stream)
 
     def finalize_device(self, stream=None):
         pcal_finalize_device(self.handle, stream)
@@ -654,6 +668,7 @@ class Server:
         _check(load().pcal_server_create(ctypes.byref(cfg), ctypes.byref(h)), "pcal_server_create")
         self.handle = h.value
         self.n_tones = {}
+        self.fmts = {}
 
     def close(self):
         if getattr(self, "handle", None):
@@ -678,16 +693,26 @@ class Server:
         sid = ctypes.c_int()
         _check(load().pcal_server_open(self.handle, ctypes.byref(d), ctypes.byref(sid)), "pcal_server_open")
         self.n_tones[sid.value] = d.N
+        self.fmts[sid.value] = {v: k for k, v in FORMATS.items()}[d.sample_format]
         return sid.value
 
+    def _host_n(self, stream: int, host: np.ndarray, n: int) -> int:
+        fmt = self.fmts.get(int(stream))
+        if fmt is None:  # not opened here: the library checks the stream id
+            if not host.flags.c_contiguous:
+                raise ValueError("host samples must be C-contiguous")
+            return int(n)
+        return host_sample_count(host, fmt, n)
+
     def submit(self, stream: int, host: np.ndarray, n: int):
-        _check(load().pcal_server_submit(self.handle, int(stream), host.ctypes.data, int(n)), "pcal_server_submit")
+        n = self._host_n(stream, host, n)
+        _check(load().pcal_server_submit(self.handle, int(stream), host.ctypes.data, n), "pcal_server_submit")
 
     def submit_many(self, streams, hosts, ns):
         k = len(streams)
         ids = (ctypes.c_int * k)(*[int(x) for x in streams])
         ptrs = (ctypes.c_void_p * k)(*[h.ctypes.data for h in hosts])
-        nn = (ctypes.c_int64 * k)(*[int(x) for x in ns])
+        nn = (ctypes.c_int64 * k)(*[self._host_n(x, h, m) for x, h, m in zip(streams, hosts, ns)])
         _check(load().pcal_server_submit_many(self.handle, k, ids, ctypes.cast(ptrs, ctypes.POINTER(ctypes.c_void_p)),
                                               nn), "pcal_server_submit_many")
 

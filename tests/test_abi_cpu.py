@@ -230,3 +230,23 @@ def test_dft_and_batch_wrappers_check_tensors():
                        ([0, _FakeDeviceTensor(100, 4)], [0, 100])]:                  # float32 for an int8 channel
         with pytest.raises(ValueError):
             pcal.Batch._check_tensors(batch, samples, n)
+
+
+def test_host_sample_count_checks_the_array():
+    count = pcal.host_sample_count
+    assert count(np.zeros(100, np.uint8), "2bit", None) == 400
+    assert count(np.zeros(100, np.int8), "i8", 60) == 60
+    assert count(np.zeros(100, np.float32), "f32", None) == 100
+    for host, fmt, n in [(np.zeros(100, np.uint8), "2bit", 404),
+                         (np.zeros(100, np.float32), "i8", None),
+                         (np.zeros(100, np.int8), "f32", None),
+                         (np.zeros((10, 20), np.int8)[:, ::2], "i8", None)]:  # not contiguous
+        with pytest.raises(ValueError):
+            count(host, fmt, n)
+    import types
+
+    srv = types.SimpleNamespace(fmts={3: "i8"})
+    assert pcal.Server._host_n(srv, 3, np.zeros(10, np.int8), 10) == 10
+    assert pcal.Server._host_n(srv, 9, np.zeros(10, np.int8), 99) == 99  # unknown stream: the library decides
+    with pytest.raises(ValueError):
+        pcal.Server._host_n(srv, 3, np.zeros(10, np.int8), 11)
