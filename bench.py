@@ -456,7 +456,7 @@ def run_gpu(args):
 
     cpu = None
     cpu_fold = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:  # the host baseline: N = 1 only
         v, dt = cpu_oracle_rate(args.cpu_sample)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"direct FP64 definition over the first {args.cpu_sample} samples ({dt:.1f} s)"}
@@ -720,7 +720,7 @@ def run_batch(args, emit=True):
                 "peak_kind": f"{peak_kind} (copy bandwidth)", "kernel": "batch_fold_kernel",
                 "algorithmic_bytes_per_launch": total_bytes}
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:  # the host baseline: N = 1 only
         v, dt = cpu_oracle_rate(args.cpu_sample)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"direct FP64 definition over the first {args.cpu_sample} samples of a 2-bit channel "
