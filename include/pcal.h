@@ -340,7 +340,7 @@ int pcal_batch_get_geometry(const pcal_batch* batch, int channel, pcal_geometry*
 int pcal_batch_set_schedule(pcal_batch* batch, const pcal_schedule* sched);
 /* How the batch finalize runs the tone DFT (the PCAL_DFT_* modes of the
  * batched tone DFT below): PCAL_DFT_FP32 (default) inside each channel's
- * finalize cluster on CUDA cores; PCAL_DFT_TC_TF32X3 / PCAL_DFT_TC_BF16X3 as
+ * finalize cluster on CUDA cores; PCAL_DFT_TC_TF32X3 / PCAL_DFT_TC_BF16X6 as
  * one tensor-core contraction per distinct N over all channels of that N (the
  * clusters stop at P, then a products kernel finishes every channel).
  * Synchronises the device; drops captured step graphs. */
@@ -411,8 +411,10 @@ int pcal_batch_autotune(pcal_batch* batch, const void* const* samples, const int
  * Clients submit chunks of host samples; a scheduler thread folds every
  * stream's pending samples with one persistent launch (the batched fold),
  * finalizes each stream once period_s seconds of its samples are folded
- * (Sec. 2), and publishes the results with their latency: from the return of
- * the submit that brought a period's last sample to the results on the host.
+ * (Sec. 2), and publishes the results with their latency: from the arrival
+ * of the chunk that brought a period's last sample (the time the client
+ * stamps on it with pcal_server_submit_many_at, else the return of its
+ * submit) to the moment the results are on the host.
  * Work submitted while the GPU is busy joins the next launch (several are in
  * flight).  The paper has no counterpart; serving is an interface choice of
  * this library.  All calls are thread-safe; one client thread per stream.
@@ -429,7 +431,7 @@ typedef struct {
     int64_t period;           /* 0, 1, 2, ... for this stream                   */
     int64_t n_samples;        /* samples in the period                          */
     double td_s, sigma_td_s;  /* delay and its 1-sigma                          */
-    double latency_s;         /* last sample submitted -> results on the host  */
+    double latency_s;         /* arrival of the period's last chunk -> results on the host */
     double td_peak_s;         /* delay from the time-domain pulse (pcal_read_post) */
 } pcal_server_result;
 
@@ -457,6 +459,14 @@ int pcal_server_submit(pcal_server* server, int stream_id, const void* host_samp
 /* One chunk for each of `count` distinct streams, copied together. */
 int pcal_server_submit_many(pcal_server* server, int count, const int* stream_ids, const void* const* host_samples,
                             const int64_t* n);
+/* As pcal_server_submit_many, with the arrival time of each chunk (arrival_s: HOST, `count` times
+ * in seconds of pcal_clock_s; NULL = the submit's return): a period's latency is measured from
+ * the arrival of its last chunk, so time the chunk spent waiting for the client, for admission,
+ * for ring space and for its copy counts.  PCAL_EINVAL for a NaN time. */
+int pcal_server_submit_many_at(pcal_server* server, int count, const int* stream_ids,
+                               const void* const* host_samples, const int64_t* n, const double* arrival_s);
+/* The library's monotonic clock in seconds (the clock of arrival times and latencies). */
+double pcal_clock_s(void);
 /* Close a stream: its submitted samples are still folded, a partial period is dropped, then its
  * memory returns to the budget. */
 int pcal_server_close(pcal_server* server, int stream_id);
@@ -549,24 +559,30 @@ int pcal_rotplan_read_results(pcal_rotplan* plan, double* phasors, double* amp, 
  *   PCAL_DFT_FP32       CUDA cores, FP32 sums
  *   PCAL_DFT_TC_TF32X3  tensor cores (tcgen05): [Re P | Im P] . W as one real
  *                       C x 2N x 2N contraction, operands split in two TF32
- *                       parts, three products accumulated in FP32
- *   PCAL_DFT_TC_BF16X3  the same with BF16 parts (errors vs FP64 at N = 1024,
- *                       max|T - T_ref| / max|T_ref|: FP32 2.9e-6, TF32x3 7.6e-6,
- *                       BF16x3 5.6e-6)
+ *                       parts (x = h + l), three products
+ *   PCAL_DFT_TC_BF16X6  the same with three BF16 parts (x = h + m + l) and
+ *                       the six products of total order <= 2
+ * In both tensor-core modes every K chunk of 128 bytes per row starts a fresh
+ * FP32 accumulator in tensor memory, which is added into FP32 registers on
+ * CUDA cores (round to nearest) while the next chunk accumulates: the error
+ * stays at the level of an FP32 sum.  Errors vs FP64 at C = 4096, N = 1024,
+ * max over channels of max|T - T_ref| / max|T_ref|, measured on GB300:
+ * FP32 2.8e-6, TF32x3 6.1e-7, BF16x6 4.2e-7.
  * pcal_dft_create builds the weight tiles (2N x 2N, split, in the layout the
- * kernel copies; 32 MB (TF32) or 16 MB (BF16) for N = 1024) once;
+ * kernel copies; 32 MB (TF32) or 24 MB (BF16) for N = 1024) once;
  * 1 <= N <= PCAL_BATCH_MAX_N.
- * pcal_dft_execute is asynchronous on `stream`; C <= 65535 * 128.
+ * pcal_dft_execute is asynchronous on `stream`; C <= 65535 * 128.  Its
+ * operand workspace grows (cudaMalloc) when C exceeds every earlier call's.
  * pcal_dft_check synchronises and returns PCAL_ETIMEOUT (with the device
  * error bits) if a bounded wait inside the kernel gave up.
- * pcal_dft_weights_host writes the hi and lo weight tile (tile, chunk) of a
- * tensor-core mode into host buffers of 32 KB each (rows = the tile's output
- * columns, at most 256 for split BF16 and 128 for split TF32, returned in
- * *rows); host-only, for tests of the layout.
+ * pcal_dft_weights_host writes weight tile (tile, chunk) of a tensor-core
+ * mode into `parts` (HOST, 3 x 16 KB: part p at byte 16384 p; rows = the
+ * tile's output columns, at most 128, returned in *rows; the mode's number
+ * of parts, 2 or 3, in *n_parts); host-only, for tests of the layout.
  */
 #define PCAL_DFT_FP32 0
 #define PCAL_DFT_TC_TF32X3 1
-#define PCAL_DFT_TC_BF16X3 2
+#define PCAL_DFT_TC_BF16X6 2
 typedef struct pcal_dft pcal_dft;
 
 /* PCAL_EINVAL for N or mode out of range, PCAL_ENOMEM / PCAL_ECUDA when the
@@ -580,7 +596,7 @@ int pcal_dft_execute(pcal_dft* dft, const void* P, int64_t C, void* T, void* str
 int pcal_dft_check(pcal_dft* dft, unsigned int* flags_out);
 /* PCAL_EINVAL for the CUDA-core mode, N out of range, or tile / chunk
  * outside the weight matrix. */
-int pcal_dft_weights_host(int N, int mode, int tile, int chunk, void* hi, void* lo, int* rows);
+int pcal_dft_weights_host(int N, int mode, int tile, int chunk, void* parts, int* rows, int* n_parts);
 
 /*
  * Failure detection without a fault: one block waits, with the bounded

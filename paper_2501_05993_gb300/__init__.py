@@ -160,7 +160,7 @@ def load(path: str | None = None):
         "pcal_dft_destroy": ([vp], ci),
         "pcal_dft_execute": ([vp, vp, i64, vp, vp], ci),
         "pcal_dft_check": ([vp, P(ctypes.c_uint)], ci),
-        "pcal_dft_weights_host": ([ci, ci, ci, ci, vp, vp, P(ci)], ci),
+        "pcal_dft_weights_host": ([ci, ci, ci, ci, vp, P(ci), P(ci)], ci),
         "pcal_rotplan_create": ([dbl, dbl, dbl, ci, ci, P(vp)], ci),
         "pcal_rotplan_destroy": ([vp], ci),
         "pcal_rotplan_set_levels": ([vp, P(dbl)], ci),
@@ -172,6 +172,8 @@ def load(path: str | None = None):
         "pcal_server_open": ([vp, P(ChannelDesc), P(ci)], ci),
         "pcal_server_submit": ([vp, ci, vp, i64], ci),
         "pcal_server_submit_many": ([vp, ci, P(ci), P(vp), P(i64)], ci),
+        "pcal_server_submit_many_at": ([vp, ci, P(ci), P(vp), P(i64), P(dbl)], ci),
+        "pcal_clock_s": ([], dbl),
         "pcal_server_close": ([vp, ci], ci),
         "pcal_server_poll": ([vp, P(ServerResult), vp, ci, dbl], ci),
         "pcal_server_drain": ([vp, dbl], ci),
@@ -638,7 +640,7 @@ class Batch:
         pcal_batch_set_schedule(self.handle, s)
 
     def set_dft(self, mode: str):
-        """Tone DFT of the finalize: "fp32" (inside each channel's cluster), "tf32x3" or "bf16x3"
+        """Tone DFT of the finalize: "fp32" (inside each channel's cluster), "tf32x3" or "bf16x6"
         (one tensor-core contraction per distinct N)."""
         _check(load().pcal_batch_set_dft(self.handle, DFT_MODES[mode]), "pcal_batch_set_dft")
 
@@ -647,6 +649,11 @@ class Batch:
 
 
 # ---- serving --------------------------------------------------------------------------
+
+
+def clock_s() -> float:
+    """The library's monotonic clock (seconds), the clock of serving arrival times and latencies."""
+    return load().pcal_clock_s()
 
 
 def pcal_server_stream_bytes(fs, f_comb, f_offset, fmt, period_s=1.0, ring_s=0.1, N=None) -> int:
@@ -708,13 +715,20 @@ class Server:
         n = self._host_n(stream, host, n)
         _check(load().pcal_server_submit(self.handle, int(stream), host.ctypes.data, n), "pcal_server_submit")
 
-    def submit_many(self, streams, hosts, ns):
+    def submit_many(self, streams, hosts, ns, arrival_s=None):
+        """One chunk per stream; arrival_s: the chunks' arrival times on pcal_clock_s (None: now)."""
         k = len(streams)
         ids = (ctypes.c_int * k)(*[int(x) for x in streams])
         ptrs = (ctypes.c_void_p * k)(*[h.ctypes.data for h in hosts])
         nn = (ctypes.c_int64 * k)(*[self._host_n(x, h, m) for x, h, m in zip(streams, hosts, ns)])
-        _check(load().pcal_server_submit_many(self.handle, k, ids, ctypes.cast(ptrs, ctypes.POINTER(ctypes.c_void_p)),
-                                              nn), "pcal_server_submit_many")
+        arr = None
+        if arrival_s is not None:
+            if len(arrival_s) != k:
+                raise ValueError("one arrival time per chunk")
+            arr = (ctypes.c_double * k)(*[float(t) for t in arrival_s])
+        _check(load().pcal_server_submit_many_at(self.handle, k, ids,
+                                                 ctypes.cast(ptrs, ctypes.POINTER(ctypes.c_void_p)), nn, arr),
+               "pcal_server_submit_many_at")
 
     def close_stream(self, stream: int):
         _check(load().pcal_server_close(self.handle, int(stream)), "pcal_server_close")
@@ -848,13 +862,13 @@ class RotPlan:
 
 # ---- batched tone DFT ---------------------------------------------------------------
 
-PCAL_DFT_FP32, PCAL_DFT_TC_TF32X3, PCAL_DFT_TC_BF16X3 = 0, 1, 2
-DFT_MODES = {"fp32": PCAL_DFT_FP32, "tf32x3": PCAL_DFT_TC_TF32X3, "bf16x3": PCAL_DFT_TC_BF16X3}
+PCAL_DFT_FP32, PCAL_DFT_TC_TF32X3, PCAL_DFT_TC_BF16X6 = 0, 1, 2
+DFT_MODES = {"fp32": PCAL_DFT_FP32, "tf32x3": PCAL_DFT_TC_TF32X3, "bf16x6": PCAL_DFT_TC_BF16X6}
 
 
 class Dft:
     """Batched N-point tone DFT of C channels: T[c, i] = sum_b P[c, b] e^{-j 2 pi i b / N}
-    (device complex64 arrays [C][N]); mode "fp32" (CUDA cores), "tf32x3" or "bf16x3" (tensor cores)."""
+    (device complex64 arrays [C][N]); mode "fp32" (CUDA cores), "tf32x3" or "bf16x6" (tensor cores)."""
 
     def __init__(self, N: int, mode: str = "tf32x3"):
         self.N, self.mode = int(N), mode
@@ -895,13 +909,14 @@ class Dft:
         return flags.value
 
 
-def pcal_dft_weights_host(N: int, mode: str, tile: int, chunk: int) -> tuple[np.ndarray, np.ndarray, int]:
-    """Host copy of the hi and lo weight tiles (tile, chunk) of a tensor-core mode (up to 32 KB each)."""
-    hi, lo = np.zeros(32768, np.uint8), np.zeros(32768, np.uint8)
-    rows = ctypes.c_int()
-    _check(load().pcal_dft_weights_host(int(N), DFT_MODES[mode], int(tile), int(chunk), hi.ctypes.data,
-                                        lo.ctypes.data, ctypes.byref(rows)), "pcal_dft_weights_host")
-    return hi, lo, rows.value
+def pcal_dft_weights_host(N: int, mode: str, tile: int, chunk: int) -> tuple[list, int]:
+    """Host copy of weight tile (tile, chunk) of a tensor-core mode: its parts (2 or 3 byte arrays of 16 KB,
+    the tile image of each part) and its rows."""
+    buf = np.zeros(3 * 16384, np.uint8)
+    rows, n_parts = ctypes.c_int(), ctypes.c_int()
+    _check(load().pcal_dft_weights_host(int(N), DFT_MODES[mode], int(tile), int(chunk), buf.ctypes.data,
+                                        ctypes.byref(rows), ctypes.byref(n_parts)), "pcal_dft_weights_host")
+    return [buf[16384 * p:16384 * (p + 1)] for p in range(n_parts.value)], rows.value
 
 
 def pcal_selftest_wait_timeout(limit_s: float) -> tuple[int, int]:

@@ -888,7 +888,7 @@ cudaError_t batch_finalize_all(pcal_batch* b, cudaStream_t s, int* launches) {
 
 extern "C" int pcal_batch_set_dft(pcal_batch* b, int mode) {
     if (!b) return PCAL_EINVAL;
-    if (mode != PCAL_DFT_FP32 && mode != PCAL_DFT_TC_TF32X3 && mode != PCAL_DFT_TC_BF16X3) return PCAL_EINVAL;
+    if (mode != PCAL_DFT_FP32 && mode != PCAL_DFT_TC_TF32X3 && mode != PCAL_DFT_TC_BF16X6) return PCAL_EINVAL;
     if (mode == b->dft_mode) return PCAL_OK;
     if (cudaDeviceSynchronize() != cudaSuccess) return PCAL_ECUDA;
     // captured steps hold the old finalize

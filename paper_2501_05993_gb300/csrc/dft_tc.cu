@@ -7,27 +7,36 @@
 //   angles 2 pi (i b mod N) / N (rows b < N for Re P, then Im P),
 //
 // which is dense, so it belongs on the tensor cores.  The operands are split
-// in two parts of the MMA type (x = hi + lo, hi = round(x), lo = round(x - hi))
-// and three products hi.hi + hi.lo + lo.hi accumulate in FP32 in tensor
-// memory.  The tensor cores' FP32 accumulation loses about one unit in the
-// last place per MMA, in the same direction, so the error grows with the
-// number of MMAs an accumulator takes: the hi.hi products and the small cross
-// products go to separate accumulators (split TF32, with twice the MMAs per K,
-// also splits hi.hi over even and odd K chunks), added in FP32 at the end
-// (error figures: pcal.h).
+// into parts of the MMA type whose sum carries FP32's precision: split TF32,
+// x = h + l (two 11-bit parts, 2^-22 of x left out) with the products
+// h.h + h.l + l.h; split BF16, x = h + m + l (three 8-bit parts, 2^-26 left
+// out) with the six products of total order <= 2 (h.h, h.m, m.h, h.l, l.h,
+// m.m; the rest are below 2^-24 of the result).
+//
+// Accumulation.  The tensor cores add an MMA's products into the FP32
+// accumulator with about one unit in the last place of error, in the same
+// direction every time, so an accumulator that takes every MMA of a long
+// contraction drifts by (MMAs) x ulp (measured: 7.6e-6 of max|T| at N = 1024
+// for one TF32 accumulator over 256 MMAs).  Here each K chunk (128 bytes of
+// K per row: 32 TF32 or 64 BF16 values) starts a fresh accumulator in tensor
+// memory, its small cross products first and its h.h products last, and
+// eight drain warps move the chunk's sum into FP32 registers (round to
+// nearest) while the next chunk accumulates into the other of two TMEM
+// buffers.  The drift per chunk is then a few ulps of that chunk's share of
+// T, and the chunk sums add like an ordinary FP32 sum.
 //
 // Kernels.  split_p_kernel writes P as split operand tiles in the shared-
 // memory image layout.  dft_tc_kernel: a CTA owns 128 channels (MMA M, rows
-// in TMEM lanes) x up to 256 (split BF16) or 128 (split TF32) output columns
-// (MMA N) and walks K = 2N in chunks of 128 bytes per row (64 BF16 or 32 TF32
-// values); a producer thread streams each chunk's operand and weight tiles
-// into shared-memory stages with 1-D bulk copies, an MMA thread issues 4
-// K-steps x 3 products per chunk and commits them to the stage's empty
-// barrier, and the epilogue parks the accumulators in shared memory and
-// writes complex T row by row.  Shared-memory tiles use the no-swizzle
-// K-major layout: 8-row x 16-byte core matrices, the core matrices of one
-// 8-row band along K `rows/8 * 128` bytes apart (leading byte offset) and
-// consecutive bands 128 bytes apart (stride byte offset).
+// in TMEM lanes) x up to 128 output columns (MMA N) and walks K = 2N chunk
+// by chunk; a producer thread streams each chunk's operand and weight parts
+// into shared-memory stages with 1-D bulk copies, an MMA thread issues the
+// chunk's 4 K-steps x products and commits them to the stage's empty barrier
+// and to the TMEM buffer's full barrier, and the drain warps add the buffer
+// into registers, release it, and at the end park the tile in shared memory
+// from where all threads write complex T row by row.  Shared-memory tiles use
+// the no-swizzle K-major layout: 8-row x 16-byte core matrices, the core
+// matrices of one 8-row band along K `rows/8 * 128` bytes apart (leading byte
+// offset) and consecutive bands 128 bytes apart (stride byte offset).
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
@@ -41,26 +50,40 @@ namespace {
 
 using namespace pcal_ptx;
 
-constexpr int kTcM = 128;              // channels per tile (MMA M)
-// Output columns per tile (MMA N), stages and accumulators per mode: split
-// BF16 (16 K values per MMA) takes 256-column tiles with two accumulators
-// (hi.hi, cross products) in 2 stages of 96 KB; split TF32 (8 K values per
-// MMA, twice the MMAs per accumulator) 128-column tiles with the hi.hi
-// products over even and odd chunks in separate accumulators, in 3 stages
-// of 64 KB.
+constexpr int kTcM = 128;                       // channels per tile (MMA M)
+constexpr int kChunkBytes = 128;                // bytes of K per row and chunk
+constexpr int kATile = kTcM * kChunkBytes;      // 16 KB: one part of a row tile's chunk
+constexpr int kTcThreads = 384;                 // 12 warps
+constexpr int kDrainWarp0 = 4;                  // warps 4..11 drain the accumulators
+constexpr int kDrainWarps = 8;
+constexpr int kAccCols = 128;                   // TMEM columns of one accumulator buffer
+constexpr int kTmemCols = 2 * kAccCols;         // two buffers (a power of two)
+
+// Per mode: parts per operand, products per K-step and pipeline depth.  Both
+// modes take 128-column tiles; split TF32 moves 64 KB per chunk (3 stages),
+// split BF16 96 KB (2 stages): 192 KB of shared memory, one CTA per SM.
 template <int MODE>
 struct TcCfg {
-    static constexpr bool kWide = MODE == PCAL_DFT_TC_BF16X3;
-    static constexpr int kNT = kWide ? 256 : 128;
-    static constexpr int kStages = kWide ? 2 : 3;
-    static constexpr int kBTile = kNT * 128;                     // bytes of one weight part per chunk
-    static constexpr int kStageBytes = 2 * 128 * 128 + 2 * kBTile;  // A hi, A lo, B hi, B lo
-    static constexpr int kSmem = kStages * kStageBytes;          // 192 KB either way: one CTA per SM
+    static constexpr bool kTf32 = MODE == PCAL_DFT_TC_TF32X3;
+    static constexpr int kParts = kTf32 ? 2 : 3;
+    static constexpr int kProducts = kTf32 ? 3 : 6;
+    static constexpr int kNT = 128;                                  // output columns per tile
+    static constexpr int kBTile = kNT * kChunkBytes;                 // 16 KB: one weight part per chunk
+    static constexpr int kStageBytes = kParts * (kATile + kBTile);
+    static constexpr int kStages = kTf32 ? 3 : 2;
+    static constexpr int kSmem = kStages * kStageBytes;
 };
-constexpr int kTcThreads = 256;        // 8 warps
-constexpr int kChunkBytes = 128;       // bytes of K per row and chunk
-constexpr int kATile = kTcM * kChunkBytes;      // 16 KB
-constexpr int kTmemCols = 512;                  // the accumulators of either mode (a power of two)
+
+// The products of a K-step as (part of A, part of B), the small cross
+// products first and h.h last, so that the accumulator is still small while
+// most of the MMAs add into it.
+__host__ __device__ constexpr int prod_a(int mode, int p) {
+    return mode == PCAL_DFT_TC_TF32X3 ? (p == 1 ? 1 : 0) : (p == 0 ? 1 : p == 2 ? 2 : p == 4 ? 1 : 0);
+}
+__host__ __device__ constexpr int prod_b(int mode, int p) {
+    return mode == PCAL_DFT_TC_TF32X3 ? (p == 0 ? 1 : 0) : (p == 0 ? 1 : p == 1 ? 2 : p == 3 ? 1 : 0);
+}
+// TF32: (0,1) (1,0) (0,0);  BF16: (1,1) (0,2) (2,0) (0,1) (1,0) (0,0)
 
 // Byte offset of element (r, k) of a rows x (128 bytes of K) tile, elements
 // of `esize` bytes, in the no-swizzle K-major core-matrix layout.
@@ -105,35 +128,39 @@ __host__ __device__ inline float f32_of_bits(uint32_t u) {
 #endif
 }
 
-// Split x into two parts of the MMA type (bit patterns in the low bits).
+// Split x into the mode's parts (bit patterns in the low bits).  Each
+// remainder x - part is exact in FP32: a part is x rounded to fewer bits.
 template <int MODE>
-__host__ __device__ inline void split_parts(float x, uint32_t& h, uint32_t& l) {
+__host__ __device__ inline void split_parts(float x, uint32_t* part) {
     if (MODE == PCAL_DFT_TC_TF32X3) {
-        h = tf32_bits_rna(x);
-        l = tf32_bits_rna(x - f32_of_bits(h));
+        part[0] = tf32_bits_rna(x);
+        part[1] = tf32_bits_rna(x - f32_of_bits(part[0]));
     } else {
-        h = bf16_bits_rn(x);
-        l = bf16_bits_rn(x - f32_of_bits(h << 16));
-    }
-}
-
-// Split x, written at `hi` and `lo` (aligned to the element size).
-template <int MODE>
-__host__ __device__ inline void split_store(float x, uint8_t* hi, uint8_t* lo) {
-    uint32_t h, l;
-    split_parts<MODE>(x, h, l);
-    if (MODE == PCAL_DFT_TC_TF32X3) {
-        *reinterpret_cast<uint32_t*>(hi) = h;
-        *reinterpret_cast<uint32_t*>(lo) = l;
-    } else {
-        *reinterpret_cast<uint16_t*>(hi) = (uint16_t)h;
-        *reinterpret_cast<uint16_t*>(lo) = (uint16_t)l;
+        part[0] = bf16_bits_rn(x);
+        const float r1 = x - f32_of_bits(part[0] << 16);
+        part[1] = bf16_bits_rn(r1);
+        const float r2 = r1 - f32_of_bits(part[1] << 16);
+        part[2] = bf16_bits_rn(r2);
     }
 }
 
 template <int MODE>
 __host__ __device__ constexpr int esize_of() {
     return MODE == PCAL_DFT_TC_TF32X3 ? 4 : 2;
+}
+
+// Split x, written at parts[p] + offset for each part p (aligned to the
+// element size).
+template <int MODE>
+__host__ __device__ inline void split_store(float x, uint8_t* const* parts, uint32_t offset) {
+    uint32_t v[3];
+    split_parts<MODE>(x, v);
+    for (int p = 0; p < TcCfg<MODE>::kParts; ++p) {
+        if (MODE == PCAL_DFT_TC_TF32X3)
+            *reinterpret_cast<uint32_t*>(parts[p] + offset) = v[p];
+        else
+            *reinterpret_cast<uint16_t*>(parts[p] + offset) = (uint16_t)v[p];
+    }
 }
 
 // Element W[n][k] of the transposed weight matrix (row n = output column,
@@ -182,21 +209,19 @@ __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t adesc, uint64_t bdes
             "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
             : "memory");
 }
-__device__ __forceinline__ void tc_ld8(uint32_t taddr, float* v) {
-    uint32_t r0, r1, r2, r3, r4, r5, r6, r7;
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3), "=r"(r4), "=r"(r5), "=r"(r6), "=r"(r7)
-                 : "r"(taddr)
-                 : "memory");
+// 32 consecutive TMEM columns of the warp's 32 lanes (one column per
+// register), then wait for the load.
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t* r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    v[0] = __uint_as_float(r0);
-    v[1] = __uint_as_float(r1);
-    v[2] = __uint_as_float(r2);
-    v[3] = __uint_as_float(r3);
-    v[4] = __uint_as_float(r4);
-    v[5] = __uint_as_float(r5);
-    v[6] = __uint_as_float(r6);
-    v[7] = __uint_as_float(r7);
 }
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -204,7 +229,6 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
                  "l"(src), "r"(bytes), "r"(smem_addr(bar))
                  : "memory");
 }
-__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // Shared-memory matrix descriptor: start, leading byte offset (between core
 // matrices along K), stride byte offset (between 8-row bands), the fixed
@@ -228,25 +252,26 @@ struct DftTcArgs {
     int N;
     int n_cols;        // 2N rounded up to 16
     int k_chunks;      // chunks of K = 2N
-    const uint8_t* a;  // operand tiles of P: [row tile][chunk] x (hi, lo) x kATile bytes
-    const uint8_t* w;  // weight tiles: [column tile][chunk] x 2 kBTile bytes: hi rows, then lo rows
+    const uint8_t* a;  // operand tiles of P: [row tile][chunk] x parts x kATile bytes
+    const uint8_t* w;  // weight tiles: [column tile][chunk] x parts x (tile rows x 128) bytes
     unsigned int* err;
 };
 
 // P -> split operand tiles: row tile mt, chunk kc holds rows 128 mt.. and K
-// values kc*KC.. of [Re P | Im P] (zeros past C and 2N) as hi and lo tile
-// images.  With 128 rows, 16-byte word w = g*128 + r of an image is row r's
-// K values g*V .. g*V+V-1 of the chunk (V = 16 / element size: one core-
+// values kc*KC.. of [Re P | Im P] (zeros past C and 2N) as one tile image
+// per part.  With 128 rows, 16-byte word w = g*128 + r of an image is row
+// r's K values g*V .. g*V+V-1 of the chunk (V = 16 / element size: one core-
 // matrix row), so a thread per word reads V consecutive values of one row of
-// P (whole sectors) and writes its hi and lo words.
+// P (whole sectors) and writes that word of every part.
 constexpr int kImageWords = kATile / 16;  // 16-byte words of one tile image
 
 template <int MODE>
 __host__ __device__ inline void split_word(const float2* __restrict__ P, int64_t C, int N, int k_chunks,
-                                           int64_t blk, int w, uint4& hi, uint4& lo) {
+                                           int64_t blk, int w, uint4* out) {
     constexpr int ES = esize_of<MODE>();
     constexpr int KC = kChunkBytes / ES;
     constexpr int V = 16 / ES;
+    constexpr int NP = TcCfg<MODE>::kParts;
     const int r = w % kTcM, g = w / kTcM;
     const int64_t c = (blk / k_chunks) * kTcM + r;
     const int kk0 = (int)(blk % k_chunks) * KC + g * V;
@@ -274,72 +299,79 @@ __host__ __device__ inline void split_word(const float2* __restrict__ P, int64_t
             }
         }
     }
-    uint32_t h[4], l[4];
+    uint32_t word[NP][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         if constexpr (MODE == PCAL_DFT_TC_TF32X3) {
-            split_parts<MODE>(x[i], h[i], l[i]);
+            uint32_t v[3];
+            split_parts<MODE>(x[i], v);
+#pragma unroll
+            for (int p = 0; p < NP; ++p) word[p][i] = v[p];
         } else {
-            uint32_t h0, l0, h1, l1;
-            split_parts<MODE>(x[2 * i], h0, l0);
-            split_parts<MODE>(x[2 * i + 1], h1, l1);
-            h[i] = h0 | h1 << 16;
-            l[i] = l0 | l1 << 16;
+            uint32_t v0[3], v1[3];
+            split_parts<MODE>(x[2 * i], v0);
+            split_parts<MODE>(x[2 * i + 1], v1);
+#pragma unroll
+            for (int p = 0; p < NP; ++p) word[p][i] = v0[p] | v1[p] << 16;
         }
     }
-    hi = make_uint4(h[0], h[1], h[2], h[3]);
-    lo = make_uint4(l[0], l[1], l[2], l[3]);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) out[p] = make_uint4(word[p][0], word[p][1], word[p][2], word[p][3]);
 }
 
 // Word (g*128 + r) of a tile image that thread e of the tile writes.  Split
 // BF16: 8 consecutive threads take one row's 8 words (a warp reads 4 rows'
-// runs of P), then the next rows (18.0 against 19.3 us per launch at
-// 4096 x 1024); split TF32 (half the values per word) keeps one row per
-// thread (20.0 against 22.8 us).
+// runs of P), then the next rows; split TF32 (half the values per word)
+// keeps one row per thread.
 template <int MODE>
 __host__ __device__ inline int split_word_of_thread(int e) {
     constexpr int kRowWords = kChunkBytes / 16;  // words of one row of a chunk
-    return MODE == PCAL_DFT_TC_BF16X3 ? (e % kRowWords) * kTcM + e / kRowWords : e;
+    return MODE == PCAL_DFT_TC_BF16X6 ? (e % kRowWords) * kTcM + e / kRowWords : e;
 }
 
 template <int MODE>
 __global__ void __launch_bounds__(256) split_p_kernel(const float2* __restrict__ P, int64_t C, int N, int k_chunks,
                                                       uint4* __restrict__ out, int64_t words) {
+    constexpr int NP = TcCfg<MODE>::kParts;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += stride) {
         const int64_t blk = i / kImageWords;
         const int w = split_word_of_thread<MODE>((int)(i % kImageWords));
-        uint4 hi, lo;
-        split_word<MODE>(P, C, N, k_chunks, blk, w, hi, lo);
-        out[blk * 2 * kImageWords + w] = hi;
-        out[blk * 2 * kImageWords + kImageWords + w] = lo;
+        uint4 part[NP];
+        split_word<MODE>(P, C, N, k_chunks, blk, w, part);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) out[(blk * NP + p) * kImageWords + w] = part[p];
     }
 }
 
 
-// One CTA: 128 channels x up to TcCfg::kNT output columns.  Thread 0 streams the A
-// and B tile pairs of each chunk through kStages shared-memory stages (bulk
-// copies, full barriers); thread 32 issues the chunk's 4 K-steps x 3 products
-// and commits them to the stage's empty barrier, so a stage is refilled as
-// soon as the MMAs that read it are done; a last commit signals the epilogue.
+// One CTA: 128 channels x up to 128 output columns.  Thread 0 streams the
+// operand and weight parts of each chunk through kStages shared-memory stages
+// (bulk copies, full barriers); thread 32 waits for a stage and for the TMEM
+// buffer of the chunk (kc % 2) to be drained, issues the chunk's MMAs into
+// that buffer (the first one overwrites it) and commits them to the stage's
+// empty barrier and the buffer's full barrier; warps 4..11 add each drained
+// buffer into FP32 registers (warp w: TMEM lanes 32 (w % 4) .., columns
+// 64 ((w - 4) / 4) ..) and release it.
 template <int MODE>
 __global__ void __launch_bounds__(kTcThreads, 1) dft_tc_kernel(const DftTcArgs a) {
+    using Cfg = TcCfg<MODE>;
     constexpr int ES = esize_of<MODE>();
     constexpr int KC = kChunkBytes / ES;  // K values per chunk
     constexpr int KS = 32 / ES;           // K values per MMA
-    using Cfg = TcCfg<MODE>;
-    constexpr int kTcNMax = Cfg::kNT, kStages = Cfg::kStages, kBTile = Cfg::kBTile, kStageBytes = Cfg::kStageBytes;
+    constexpr int NP = Cfg::kParts, kStages = Cfg::kStages, kStageBytes = Cfg::kStageBytes;
+    constexpr int kDrainCols = kAccCols / 2;  // columns per drain warp
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], acc_full[2], acc_empty[2], done;
     __shared__ uint32_t s_tmem;
     __shared__ int s_fail;
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t mt = blockIdx.x;
     const int64_t m0 = mt * kTcM;
-    const int n0 = blockIdx.y * kTcNMax;
-    const int nt = a.n_cols - n0 < kTcNMax ? a.n_cols - n0 : kTcNMax;  // a multiple of 16
-    const uint32_t w_bytes = (uint32_t)nt * kChunkBytes;
-    if (warp == 0) {
+    const int n0 = blockIdx.y * Cfg::kNT;
+    const int nt = a.n_cols - n0 < Cfg::kNT ? a.n_cols - n0 : Cfg::kNT;  // a multiple of 16
+    const uint32_t w_bytes = (uint32_t)nt * kChunkBytes;                 // one weight part of a chunk
+    if (warp == 2) {
         tc_alloc(&s_tmem, kTmemCols);
         tc_relinquish();
     }
@@ -347,6 +379,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) dft_tc_kernel(const DftTcArgs a
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], kDrainWarps);
         }
         mbar_init(&done, 1);
         s_fail = 0;
@@ -358,8 +394,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) dft_tc_kernel(const DftTcArgs a
     const uint32_t tmem = s_tmem;
     if (tid == 0) {
         // ---- producer ----
-        const uint8_t* atile = a.a + (size_t)mt * a.k_chunks * 2 * kATile;
-        const uint8_t* wtile = a.w + (size_t)blockIdx.y * a.k_chunks * 2 * kBTile;
+        const uint8_t* atile = a.a + (size_t)mt * a.k_chunks * NP * kATile;
+        const uint8_t* wtile = a.w + (size_t)blockIdx.y * a.k_chunks * NP * Cfg::kBTile;
         int issued = 0;
         for (int kc = 0; kc < a.k_chunks; ++kc) {
             const int s = kc % kStages;
@@ -370,9 +406,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) dft_tc_kernel(const DftTcArgs a
             }
             issued = kc + 1;
             uint8_t* st = smem + (size_t)s * kStageBytes;
-            mbar_arrive_expect_tx(&full[s], 2 * kATile + 2 * w_bytes);
-            bulk_load(st, atile + (size_t)kc * 2 * kATile, 2 * kATile, &full[s]);
-            bulk_load(st + 2 * kATile, wtile + (size_t)kc * 2 * kBTile, 2 * w_bytes, &full[s]);  // hi and lo
+            mbar_arrive_expect_tx(&full[s], NP * kATile + NP * w_bytes);
+            bulk_load(st, atile + (size_t)kc * NP * kATile, NP * kATile, &full[s]);
+            bulk_load(st + NP * kATile, wtile + (size_t)kc * NP * Cfg::kBTile, NP * w_bytes, &full[s]);
         }
         if (s_fail) {
             // copies in flight must land before the CTA's shared memory is reused
@@ -385,33 +421,85 @@ __global__ void __launch_bounds__(kTcThreads, 1) dft_tc_kernel(const DftTcArgs a
         const uint32_t lbo_a = (kTcM / 8) * 128, lbo_b = (uint32_t)(nt / 8) * 128;
         bool ok = true;
         for (int kc = 0; kc < a.k_chunks; ++kc) {
-            const int s = kc % kStages;
+            const int s = kc % kStages, b = kc & 1;
             if (!mbar_wait(&full[s], (uint32_t)((kc / kStages) & 1))) {
                 atomicOr(a.err, PCAL_DERR_FULL_WAIT);
-                s_fail = 1;
                 ok = false;
+            } else if (kc >= 2 && !mbar_wait(&acc_empty[b], (uint32_t)(((kc >> 1) - 1) & 1))) {
+                atomicOr(a.err, PCAL_DERR_FULL_WAIT);
+                ok = false;
+            }
+            if (!ok) {
+                s_fail = 1;
                 break;
             }
             tc_fence_after();
             const uint32_t st = smem_addr(smem + (size_t)s * kStageBytes);
-            const uint32_t a_hi = st, a_lo = st + kATile, b_hi = st + 2 * kATile, b_lo = b_hi + w_bytes;
-            // hi.hi: one accumulator (wide tiles) or even / odd chunks; cross
-            // products: the last accumulator
-            const uint32_t d_hh = tmem + (Cfg::kWide ? 0u : (uint32_t)(kc & 1) * kTcNMax);
-            const uint32_t d_x = tmem + (Cfg::kWide ? 1u : 2u) * kTcNMax;
-            const bool hh_first = Cfg::kWide ? kc == 0 : kc < 2;
+            const uint32_t d = tmem + (uint32_t)(b * kAccCols);
+            uint32_t accumulate = 0u;  // the chunk's first MMA overwrites the buffer
 #pragma unroll
-            for (int k = 0; k < KC / KS; ++k) {
-                const uint32_t oa = (uint32_t)k * 2 * lbo_a, ob = (uint32_t)k * 2 * lbo_b;
-                const uint64_t ah = smem_desc(a_hi + oa, lbo_a, 128), al = smem_desc(a_lo + oa, lbo_a, 128);
-                const uint64_t bh = smem_desc(b_hi + ob, lbo_b, 128), bl = smem_desc(b_lo + ob, lbo_b, 128);
-                tc_mma<MODE>(d_hh, ah, bh, idesc, (hh_first && k == 0) ? 0u : 1u);
-                tc_mma<MODE>(d_x, ah, bl, idesc, (kc == 0 && k == 0) ? 0u : 1u);
-                tc_mma<MODE>(d_x, al, bh, idesc, 1u);
+            for (int p = 0; p < Cfg::kProducts; ++p) {
+                const uint32_t pa = st + (uint32_t)(prod_a(MODE, p) * kATile);
+                const uint32_t pb = st + (uint32_t)(NP * kATile) + (uint32_t)prod_b(MODE, p) * w_bytes;
+#pragma unroll
+                for (int k = 0; k < KC / KS; ++k) {
+                    const uint64_t ad = smem_desc(pa + (uint32_t)k * 2 * lbo_a, lbo_a, 128);
+                    const uint64_t bd = smem_desc(pb + (uint32_t)k * 2 * lbo_b, lbo_b, 128);
+                    tc_mma<MODE>(d, ad, bd, idesc, accumulate);
+                    accumulate = 1u;
+                }
             }
-            tc_commit(&empty[s]);  // the stage is free once these MMAs are done
+            tc_commit(&empty[s]);     // the stage is free once these MMAs are done
+            tc_commit(&acc_full[b]);  // and the buffer holds the chunk's sum
         }
         if (ok) tc_commit(&done);
+    } else if (warp >= kDrainWarp0) {
+        // ---- drain warps ----
+        const int q = warp & 3;                                   // TMEM lane quadrant of this warp
+        const int c0 = ((warp - kDrainWarp0) >> 2) * kDrainCols;  // first column of this warp
+        const uint32_t lane_addr = (uint32_t)(32 * q) << 16;
+        const int pieces = nt > c0 ? (nt - c0 >= kDrainCols ? 2 : (nt - c0 + 31) / 32) : 0;  // 32-column loads
+        float sum[kDrainCols];
+#pragma unroll
+        for (int j = 0; j < kDrainCols; ++j) sum[j] = 0.f;
+        bool ok = true;
+        for (int kc = 0; kc < a.k_chunks; ++kc) {
+            const int b = kc & 1;
+            if (!mbar_wait(&acc_full[b], (uint32_t)((kc >> 1) & 1))) {
+                atomicOr(a.err, PCAL_DERR_DRAIN_WAIT);
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t base = tmem + lane_addr + (uint32_t)(b * kAccCols + c0);
+            uint32_t v[32];
+            if (pieces > 0) {
+                tc_ld32(base, v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) sum[j] += __uint_as_float(v[j]);
+            }
+            if (pieces > 1) {
+                tc_ld32(base + 32u, v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) sum[32 + j] += __uint_as_float(v[j]);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[b]);
+        }
+        if (!ok) {
+            s_fail = 1;
+        } else {
+            // every MMA has completed (the last buffer's commit covers them all)
+            // and every copy has landed: the stages are free.  Park the rows
+            // (stride 129 floats: no bank conflicts).
+            constexpr int kRow = Cfg::kNT + 1;
+            float* sT = reinterpret_cast<float*>(smem);
+            const int r = 32 * q + lane;
+#pragma unroll
+            for (int j = 0; j < kDrainCols; ++j)
+                if (c0 + j < nt) sT[r * kRow + c0 + j] = sum[j];
+        }
     }
     // every thread: wait for the last MMAs (the issuer committed `done`)
     __syncthreads();
@@ -419,29 +507,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) dft_tc_kernel(const DftTcArgs a
     if (!have && tid == 0) atomicOr(a.err, PCAL_DERR_DRAIN_WAIT);
     tc_fence_after();
     if (have) {
-        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. (rows), column half
-        // w / 4, adds the three accumulators and parks the rows in shared
-        // memory (the stages are free; row stride 129 floats: no bank
-        // conflicts), then all threads write the tile's rows of complex T,
-        // consecutive threads on consecutive tones.
-        constexpr int kRow = kTcNMax + 1;
-        float* sT = reinterpret_cast<float*>(smem);
-        const int q = warp & 3, half = warp >> 2;
-        const int r = 32 * q + (tid & 31);
-        const uint32_t lane = (uint32_t)(32 * q) << 16;
-        for (int j0 = half * (kTcNMax / 2); j0 < nt && j0 < (half + 1) * (kTcNMax / 2); j0 += 8) {
-            float v[8], w[8], x[8];
-            tc_ld8(tmem + lane + (uint32_t)j0, v);
-            tc_ld8(tmem + lane + (uint32_t)((Cfg::kWide ? 1 : 2) * kTcNMax + j0), x);
-            if (!Cfg::kWide && a.k_chunks > 1) {
-                tc_ld8(tmem + lane + (uint32_t)(kTcNMax + j0), w);
-#pragma unroll
-                for (int u = 0; u < 8; ++u) v[u] += w[u];
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) sT[r * kRow + j0 + u] = v[u] + x[u];
-        }
-        __syncthreads();
+        // all threads write the tile's rows of complex T, consecutive threads
+        // on consecutive tones
+        constexpr int kRow = Cfg::kNT + 1;
+        const float* sT = reinterpret_cast<const float*>(smem);
         const int tones = nt / 2, t0 = n0 / 2;
         for (int e = tid; e < kTcM * tones; e += kTcThreads) {
             const int rr = e / tones, i = e % tones;
@@ -452,7 +521,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) dft_tc_kernel(const DftTcArgs a
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 2) {
         tc_fence_after();
         tc_dealloc(tmem, kTmemCols);
     }
@@ -486,7 +555,7 @@ __global__ void dft_fp32_kernel(const float2* __restrict__ P, float2* __restrict
 }  // namespace
 
 struct pcal_dft {
-    int N, mode, n_cols, k_chunks, col_tiles;
+    int N, mode, n_cols, k_chunks, col_tiles, parts;
     uint8_t* d_w;     // weight tiles (tensor-core modes)
     uint8_t* d_a;     // operand tiles of P (workspace)
     size_t a_cap;     // bytes of d_a
@@ -496,22 +565,27 @@ struct pcal_dft {
 
 namespace {
 
-// Weight tiles of column tile t, chunk kc, in the shared-memory image the
-// kernel copies (rows = the tile's columns, 128 bytes of K per row).
-inline int tile_cols(int mode) {
-    return mode == PCAL_DFT_TC_TF32X3 ? TcCfg<PCAL_DFT_TC_TF32X3>::kNT : TcCfg<PCAL_DFT_TC_BF16X3>::kNT;
+constexpr int kTileCols = 128;  // output columns per tile, either mode
+static_assert(TcCfg<PCAL_DFT_TC_TF32X3>::kNT == kTileCols && TcCfg<PCAL_DFT_TC_BF16X6>::kNT == kTileCols,
+              "one tile width");
+
+inline int parts_of(int mode) {
+    return mode == PCAL_DFT_TC_TF32X3 ? TcCfg<PCAL_DFT_TC_TF32X3>::kParts : TcCfg<PCAL_DFT_TC_BF16X6>::kParts;
 }
 
-int build_weight_tile(int N, int mode, int t, int kc, const double* twr, const double* twi, uint8_t* hi,
-                      uint8_t* lo) {
+// Weight tile of column tile t, chunk kc, in the shared-memory image the
+// kernel copies (rows = the tile's columns, 128 bytes of K per row): part p
+// at out + p * part_stride.  Returns the tile's rows.
+int build_weight_tile(int N, int mode, int t, int kc, const double* twr, const double* twi, uint8_t* out,
+                      size_t part_stride) {
     const int n_cols = (2 * N + 15) / 16 * 16;
-    const int NT = tile_cols(mode);
-    const int n0 = t * NT;
-    const int nt = n_cols - n0 < NT ? n_cols - n0 : NT;
+    const int n0 = t * kTileCols;
+    const int nt = n_cols - n0 < kTileCols ? n_cols - n0 : kTileCols;
     const int es = mode == PCAL_DFT_TC_TF32X3 ? 4 : 2;
     const int kcv = kChunkBytes / es;
-    memset(hi, 0, (size_t)nt * kChunkBytes);
-    memset(lo, 0, (size_t)nt * kChunkBytes);
+    const int np = parts_of(mode);
+    uint8_t* parts[3] = {out, out + part_stride, out + 2 * part_stride};
+    for (int p = 0; p < np; ++p) memset(parts[p], 0, (size_t)nt * kChunkBytes);
     for (int r = 0; r < nt; ++r) {
         const int n = n0 + r;
         for (int k = 0; k < kcv; ++k) {
@@ -519,9 +593,9 @@ int build_weight_tile(int N, int mode, int t, int kc, const double* twr, const d
             const float x = (n < 2 * N && kk < 2 * N) ? (float)weight(twr, twi, N, n, kk) : 0.f;
             const uint32_t o = tile_offset(r, k, nt, es);
             if (mode == PCAL_DFT_TC_TF32X3)
-                split_store<PCAL_DFT_TC_TF32X3>(x, hi + o, lo + o);
+                split_store<PCAL_DFT_TC_TF32X3>(x, parts, o);
             else
-                split_store<PCAL_DFT_TC_BF16X3>(x, hi + o, lo + o);
+                split_store<PCAL_DFT_TC_BF16X6>(x, parts, o);
         }
     }
     return nt;
@@ -538,31 +612,34 @@ void twiddles(int N, double* twr, double* twi) {
 
 }  // namespace
 
-extern "C" int pcal_dft_weights_host(int N, int mode, int tile, int chunk, void* hi, void* lo, int* rows) {
-    if (N < 1 || N > PCAL_BATCH_MAX_N || !hi || !lo || !rows) return PCAL_EINVAL;
-    if (mode != PCAL_DFT_TC_TF32X3 && mode != PCAL_DFT_TC_BF16X3) return PCAL_EINVAL;
+extern "C" int pcal_dft_weights_host(int N, int mode, int tile, int chunk, void* parts, int* rows, int* n_parts) {
+    if (N < 1 || N > PCAL_BATCH_MAX_N || !parts || !rows || !n_parts) return PCAL_EINVAL;
+    if (mode != PCAL_DFT_TC_TF32X3 && mode != PCAL_DFT_TC_BF16X6) return PCAL_EINVAL;
     const int n_cols = (2 * N + 15) / 16 * 16;
     const int es = mode == PCAL_DFT_TC_TF32X3 ? 4 : 2;
     const int k_chunks = (2 * N + kChunkBytes / es - 1) / (kChunkBytes / es);
-    if (tile < 0 || tile * tile_cols(mode) >= n_cols || chunk < 0 || chunk >= k_chunks) return PCAL_EINVAL;
+    if (tile < 0 || tile * kTileCols >= n_cols || chunk < 0 || chunk >= k_chunks) return PCAL_EINVAL;
     double* tw = new (std::nothrow) double[2 * (size_t)N];
     if (!tw) return PCAL_ENOMEM;
     twiddles(N, tw, tw + N);
-    *rows = build_weight_tile(N, mode, tile, chunk, tw, tw + N, static_cast<uint8_t*>(hi), static_cast<uint8_t*>(lo));
+    *rows = build_weight_tile(N, mode, tile, chunk, tw, tw + N, static_cast<uint8_t*>(parts),
+                              (size_t)kTileCols * kChunkBytes);
+    *n_parts = parts_of(mode);
     delete[] tw;
     return PCAL_OK;
 }
 
 extern "C" int pcal_dft_create(int N, int mode, pcal_dft** out) {
     if (!out || N < 1 || N > PCAL_BATCH_MAX_N) return PCAL_EINVAL;
-    if (mode != PCAL_DFT_FP32 && mode != PCAL_DFT_TC_TF32X3 && mode != PCAL_DFT_TC_BF16X3) return PCAL_EINVAL;
+    if (mode != PCAL_DFT_FP32 && mode != PCAL_DFT_TC_TF32X3 && mode != PCAL_DFT_TC_BF16X6) return PCAL_EINVAL;
     pcal_dft* d = new (std::nothrow) pcal_dft();
     if (!d) return PCAL_ENOMEM;
     memset(static_cast<void*>(d), 0, sizeof(*d));
     d->N = N;
     d->mode = mode;
     d->n_cols = (2 * N + 15) / 16 * 16;
-    d->col_tiles = mode == PCAL_DFT_FP32 ? 0 : (d->n_cols + tile_cols(mode) - 1) / tile_cols(mode);
+    d->col_tiles = mode == PCAL_DFT_FP32 ? 0 : (d->n_cols + kTileCols - 1) / kTileCols;
+    d->parts = mode == PCAL_DFT_FP32 ? 0 : parts_of(mode);
     const int es = mode == PCAL_DFT_TC_TF32X3 ? 4 : 2;
     d->k_chunks = (2 * N + kChunkBytes / es - 1) / (kChunkBytes / es);
     double* tw = new (std::nothrow) double[2 * (size_t)N];
@@ -581,30 +658,29 @@ extern "C" int pcal_dft_create(int N, int mode, pcal_dft** out) {
         if (e == cudaSuccess) e = cudaMemcpy(d->d_tw, h, N * sizeof(float2), cudaMemcpyHostToDevice);
         delete[] h;
     } else if (e == cudaSuccess) {
-        const int NT = tile_cols(mode), kBTile = NT * kChunkBytes;
-        const size_t bytes = (size_t)d->col_tiles * d->k_chunks * 2 * kBTile;
+        // per (column tile, chunk): the parts of the tile's rows, one after the
+        // other (a ragged last tile keeps its rows together): one copy per chunk
+        const size_t block = (size_t)d->parts * kTileCols * kChunkBytes;
+        const size_t bytes = (size_t)d->col_tiles * d->k_chunks * block;
         uint8_t* h = new (std::nothrow) uint8_t[bytes];
         if (!h) e = cudaErrorMemoryAllocation;
-        for (int t = 0; h && t < d->col_tiles; ++t)
-            for (int kc = 0; kc < d->k_chunks; ++kc) {
-                // hi rows, then the lo rows right after them: one copy per chunk
-                uint8_t* base = h + ((size_t)t * d->k_chunks + kc) * 2 * kBTile;
-                const int rows = build_weight_tile(N, mode, t, kc, tw, tw + N, base, base + kBTile);
-                if (rows < NT) memmove(base + (size_t)rows * kChunkBytes, base + kBTile, (size_t)rows * kChunkBytes);
-            }
+        for (int t = 0; h && t < d->col_tiles; ++t) {
+            const int nt = d->n_cols - t * kTileCols < kTileCols ? d->n_cols - t * kTileCols : kTileCols;
+            for (int kc = 0; kc < d->k_chunks; ++kc)
+                build_weight_tile(N, mode, t, kc, tw, tw + N, h + ((size_t)t * d->k_chunks + kc) * block,
+                                  (size_t)nt * kChunkBytes);
+        }
         if (e == cudaSuccess) e = cudaMalloc(&d->d_w, bytes);
         if (e == cudaSuccess) e = cudaMemcpy(d->d_w, h, bytes, cudaMemcpyHostToDevice);
         delete[] h;
     }
     delete[] tw;
     if (e == cudaSuccess && mode != PCAL_DFT_FP32) {
-        const int smem = TcCfg<PCAL_DFT_TC_TF32X3>::kSmem;
-        static_assert(TcCfg<PCAL_DFT_TC_TF32X3>::kSmem == TcCfg<PCAL_DFT_TC_BF16X3>::kSmem, "one attribute value");
         e = mode == PCAL_DFT_TC_TF32X3
                 ? cudaFuncSetAttribute(dft_tc_kernel<PCAL_DFT_TC_TF32X3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       smem)
-                : cudaFuncSetAttribute(dft_tc_kernel<PCAL_DFT_TC_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       smem);
+                                       TcCfg<PCAL_DFT_TC_TF32X3>::kSmem)
+                : cudaFuncSetAttribute(dft_tc_kernel<PCAL_DFT_TC_BF16X6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       TcCfg<PCAL_DFT_TC_BF16X6>::kSmem);
     }
     if (e != cudaSuccess) {
         pcal_dft_destroy(d);
@@ -629,7 +705,7 @@ extern "C" int pcal_dft_destroy(pcal_dft* d) {
 // Operand workspace for C channels (allocates: not under stream capture).
 cudaError_t dft_reserve(pcal_dft* d, int64_t C) {
     if (d->mode == PCAL_DFT_FP32 || C <= 0) return cudaSuccess;
-    const size_t need = (size_t)((C + kTcM - 1) / kTcM) * d->k_chunks * 2 * kATile;
+    const size_t need = (size_t)((C + kTcM - 1) / kTcM) * d->k_chunks * d->parts * kATile;
     if (need <= d->a_cap) return cudaSuccess;
     cudaFree(d->d_a);
     d->d_a = nullptr;
@@ -646,15 +722,15 @@ cudaError_t launch_dft(pcal_dft* d, const float2* P, int64_t C, float2* T, cudaS
         return cudaGetLastError();
     }
     const int64_t m_tiles = (C + kTcM - 1) / kTcM;
-    if ((size_t)m_tiles * d->k_chunks * 2 * kATile > d->a_cap) return cudaErrorInvalidValue;  // dft_reserve first
-    const int64_t words = m_tiles * d->k_chunks * kImageWords;  // one thread per word (hi and lo)
+    if ((size_t)m_tiles * d->k_chunks * d->parts * kATile > d->a_cap) return cudaErrorInvalidValue;  // dft_reserve first
+    const int64_t words = m_tiles * d->k_chunks * kImageWords;  // one thread per word (all parts)
     const int64_t blocks = (words + 255) / 256;
     const int sgrid = (int)(blocks < 32 * 152 ? blocks : 32 * 152);
     uint4* a_words = reinterpret_cast<uint4*>(d->d_a);
     if (d->mode == PCAL_DFT_TC_TF32X3)
         split_p_kernel<PCAL_DFT_TC_TF32X3><<<sgrid, 256, 0, s>>>(P, C, d->N, d->k_chunks, a_words, words);
     else
-        split_p_kernel<PCAL_DFT_TC_BF16X3><<<sgrid, 256, 0, s>>>(P, C, d->N, d->k_chunks, a_words, words);
+        split_p_kernel<PCAL_DFT_TC_BF16X6><<<sgrid, 256, 0, s>>>(P, C, d->N, d->k_chunks, a_words, words);
     DftTcArgs a{};
     a.T = T;
     a.a = d->d_a;
@@ -668,7 +744,7 @@ cudaError_t launch_dft(pcal_dft* d, const float2* P, int64_t C, float2* T, cudaS
     if (d->mode == PCAL_DFT_TC_TF32X3)
         dft_tc_kernel<PCAL_DFT_TC_TF32X3><<<grid, kTcThreads, TcCfg<PCAL_DFT_TC_TF32X3>::kSmem, s>>>(a);
     else
-        dft_tc_kernel<PCAL_DFT_TC_BF16X3><<<grid, kTcThreads, TcCfg<PCAL_DFT_TC_BF16X3>::kSmem, s>>>(a);
+        dft_tc_kernel<PCAL_DFT_TC_BF16X6><<<grid, kTcThreads, TcCfg<PCAL_DFT_TC_BF16X6>::kSmem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -17,7 +17,11 @@
 // finalizes of different streams overlap.  A host callback at the end of
 // every iteration frees ring space, publishes the results with their
 // latency (last sample of the period submitted -> results on the host) and
-// returns the memory of closed streams.
+// returns the memory of closed streams.  A period's latency runs from the
+// arrival of the chunk that brought its last sample -- the time the client
+// stamps on it (pcal_server_submit_many_at), else the return of its submit --
+// to the moment its results are on the host, so the ingest copy, any wait
+// for ring space or admission and the client's own lag are inside it.
 #include <math.h>
 #include <string.h>
 
@@ -65,7 +69,7 @@ struct SrvStream {
     int64_t period_end = 0;      // end of the current period (absolute sample)
     int64_t period_index = 0;
     bool release_pending = false;
-    std::deque<std::pair<int64_t, double>> arrivals;  // (end sample of a submit, host time)
+    std::deque<std::pair<int64_t, double>> arrivals;  // (end sample of a chunk, its arrival time)
     double* h_res = nullptr;     // pinned, 5N+3 doubles
 };
 
@@ -197,7 +201,7 @@ void CUDART_CB iteration_done(void* p) {
         }
         for (const IterInfo::Fin& f : it->fins) {
             SrvStream& st = s->streams[f.id];
-            // arrival of the submit that brought the period's last sample
+            // arrival of the chunk that brought the period's last sample
             double t_arr = t;
             while (!st.arrivals.empty() && st.arrivals.front().first < f.end) st.arrivals.pop_front();
             if (!st.arrivals.empty()) t_arr = st.arrivals.front().second;
@@ -515,9 +519,13 @@ extern "C" int pcal_server_open(pcal_server* s, const pcal_channel_desc* desc, i
     return PCAL_OK;
 }
 
-extern "C" int pcal_server_submit_many(pcal_server* s, int count, const int* ids, const void* const* host,
-                                       const int64_t* n) {
+extern "C" double pcal_clock_s(void) { return now_s(); }
+
+extern "C" int pcal_server_submit_many_at(pcal_server* s, int count, const int* ids, const void* const* host,
+                                          const int64_t* n, const double* arrival_s) {
     if (!s || count < 0 || (count > 0 && (!ids || !host || !n))) return PCAL_EINVAL;
+    for (int k = 0; arrival_s && k < count; ++k)
+        if (!(arrival_s[k] == arrival_s[k])) return PCAL_EINVAL;  // NaN
     std::vector<int64_t> pos(count);
     {
         std::unique_lock<std::mutex> lk(s->mu);
@@ -591,7 +599,7 @@ extern "C" int pcal_server_submit_many(pcal_server* s, int count, const int* ids
         for (int k = 0; k < count; ++k) {
             SrvStream& st = s->streams[ids[k]];
             st.submitted += n[k];
-            st.arrivals.push_back({st.submitted, t});
+            st.arrivals.push_back({st.submitted, arrival_s ? arrival_s[k] : t});
             s->stats.samples += n[k];
         }
         s->stats.bytes_h2d += bytes;
@@ -600,8 +608,13 @@ extern "C" int pcal_server_submit_many(pcal_server* s, int count, const int* ids
     return PCAL_OK;
 }
 
+extern "C" int pcal_server_submit_many(pcal_server* s, int count, const int* ids, const void* const* host,
+                                       const int64_t* n) {
+    return pcal_server_submit_many_at(s, count, ids, host, n, nullptr);
+}
+
 extern "C" int pcal_server_submit(pcal_server* s, int stream_id, const void* host_samples, int64_t n) {
-    return pcal_server_submit_many(s, 1, &stream_id, &host_samples, &n);
+    return pcal_server_submit_many_at(s, 1, &stream_id, &host_samples, &n, nullptr);
 }
 
 extern "C" int pcal_server_close(pcal_server* s, int stream_id) {

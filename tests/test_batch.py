@@ -122,12 +122,11 @@ def test_batch_bins_and_phasors(pcal):
             check_results(b, c, ch, h)
 
 
-@pytest.mark.parametrize("mode", ["tf32x3", "bf16x3"])
+@pytest.mark.parametrize("mode", ["tf32x3", "bf16x6"])
 def test_batch_tensor_core_dft(pcal, mode):
     """The finalize with the tone DFT as one tensor-core contraction per N: every channel's phasors and
-    post-processing within the stated tolerance of the oracle; the delay within 1e-2 sigma_td (the split
-    contraction keeps ~1e-6 of the phasors: on the strongest combs here, sigma_td ~ 7e-13 s, that moves
-    the delay by ~1e-3 sigma, where the CUDA-core FP32 DFT stays below 1e-3)."""
+    post-processing within the stated tolerance of the oracle, and the delay within 1e-3 sigma_td, the bound
+    of the CUDA-core paths (on the strongest combs here sigma_td ~ 7e-13 s)."""
     hosts = make_inputs(CHANNELS, seed=9)
     keep, ptrs = upload(CHANNELS, hosts)
     with pcal.Batch([c[:4] for c in CHANNELS]) as b:
@@ -140,7 +139,7 @@ def test_batch_tensor_core_dft(pcal, mode):
             if ch[4]:
                 pr = oracle.products(oracle.tones_from_bins(oracle.bins(h, ch[3], 0, int(b.geometry[c].L)),
                                                             *ch[:3]), ch[4], *ch[:3])
-                assert abs(res["td"] - pr["td"]) <= 1e-2 * pr["sigma_td"], (c, abs(res["td"] - pr["td"]) / pr["sigma_td"])
+                assert abs(res["td"] - pr["td"]) <= 1e-3 * pr["sigma_td"], (c, abs(res["td"] - pr["td"]) / pr["sigma_td"])
         # a second period in the same mode, then back to the CUDA-core DFT
         hosts2 = make_inputs(CHANNELS, seed=10, n0=[c[4] for c in CHANNELS])
         keep2, ptrs2 = upload(CHANNELS, hosts2)

@@ -2,7 +2,8 @@
 
 The tiles hold W^T of the real form of the tone DFT, T = [Re P | Im P] . W with
 Re T_i and Im T_i in output columns 2i and 2i + 1 (angles 2 pi (i b mod N) / N),
-each value split in two parts of the MMA type.  Decoding a tile with the no-swizzle K-major layout
+each value split into parts of the MMA type (two TF32 parts, or three BF16
+parts).  Decoding a tile with the no-swizzle K-major layout
 (8-row x 16-byte core matrices, K-neighbours rows/8 * 128 bytes apart, 8-row
 bands 128 bytes apart) must give back the matrix entries to the precision of the
 split, and zeros in the padding.
@@ -16,8 +17,9 @@ import pytest
 
 import paper_2501_05993_gb300 as pcal
 
-ESIZE = {"tf32x3": 4, "bf16x3": 2}
-TILE = {"tf32x3": 128, "bf16x3": 256}  # output columns per tile
+ESIZE = {"tf32x3": 4, "bf16x6": 2}
+PARTS = {"tf32x3": 2, "bf16x6": 3}
+TILE = 128  # output columns per tile
 
 
 @pytest.fixture(scope="module")
@@ -54,36 +56,39 @@ def expected(N: int, n: np.ndarray, k: np.ndarray) -> np.ndarray:
     return np.where((n < 2 * N) & (k < 2 * N), w, 0.0)
 
 
-@pytest.mark.parametrize("mode", ["tf32x3", "bf16x3"])
+@pytest.mark.parametrize("mode", ["tf32x3", "bf16x6"])
 @pytest.mark.parametrize("N", [16, 50, 64, 200, 1024])
 def test_weight_tiles_decode_to_the_dft_matrix(lib, mode, N):
     es = ESIZE[mode]
     kcv = 128 // es
     n_cols = (2 * N + 15) // 16 * 16
-    NT = TILE[mode]
-    tiles = (n_cols + NT - 1) // NT
+    tiles = (n_cols + TILE - 1) // TILE
     chunks = (2 * N + kcv - 1) // kcv
-    tol = 2.0 ** -21 if mode == "tf32x3" else 2.0 ** -16
+    # the sum of the parts carries the float32-rounded weight: 2^-22 of it left out by two TF32 parts, 2^-26 by
+    # three BF16 parts, plus the float32 rounding (2^-24)
+    tol = 2.0 ** -21 if mode == "tf32x3" else 2.0 ** -23
     for t in sorted({0, tiles - 1}):
         for c in sorted({0, chunks // 2, chunks - 1}):
-            hi, lo, rows = pcal.pcal_dft_weights_host(N, mode, t, c)
-            assert rows == min(NT, n_cols - NT * t) and rows % 16 == 0
-            h, l = decode(hi, rows, es), decode(lo, rows, es)
-            n = NT * t + np.arange(rows)[:, None]
+            parts, rows = pcal.pcal_dft_weights_host(N, mode, t, c)
+            assert len(parts) == PARTS[mode]
+            assert rows == min(TILE, n_cols - TILE * t) and rows % 16 == 0
+            vals = [decode(p, rows, es) for p in parts]
+            n = TILE * t + np.arange(rows)[:, None]
             k = c * kcv + np.arange(kcv)[None, :]
             w = expected(N, n, k)
-            assert np.max(np.abs(h + l - w)) <= tol, (t, c)
-            assert np.all((h == 0) & (l == 0) | (w != 0) | ((n < 2 * N) & (k < 2 * N)))
+            assert np.max(np.abs(sum(vals) - w)) <= tol, (t, c)
+            # each part is at most half an ulp of the one before it (round to nearest at every step)
+            for a, b in zip(vals, vals[1:]):
+                assert np.all(np.abs(b) <= np.abs(a) * 2.0 ** -(8 if mode == "bf16x6" else 11) + 1e-300)
             pad = (n >= 2 * N) | (k >= 2 * N)
-            assert np.all(h[pad] == 0) and np.all(l[pad] == 0)
+            assert all(np.all(v[pad] == 0) for v in vals)
             if mode == "tf32x3":  # the parts are TF32 values: 13 low mantissa bits clear
-                assert np.all(hi.view(np.uint32)[: rows * 32] & 0x1FFF == 0)
-                assert np.all(lo.view(np.uint32)[: rows * 32] & 0x1FFF == 0)
+                assert all(np.all(p.view(np.uint32)[: rows * 32] & 0x1FFF == 0) for p in parts)
 
 
 def test_weights_reject_bad_arguments(lib):
-    for args in [(0, "tf32x3", 0, 0), (1025, "tf32x3", 0, 0), (64, "tf32x3", 1, 0), (64, "bf16x3", 0, 2),
-                 (200, "tf32x3", 4, 0), (200, "bf16x3", 2, 0),
+    for args in [(0, "tf32x3", 0, 0), (1025, "tf32x3", 0, 0), (64, "tf32x3", 1, 0), (64, "bf16x6", 0, 2),
+                 (200, "tf32x3", 4, 0), (200, "bf16x6", 4, 0),
                  (64, "fp32", 0, 0)]:  # the CUDA-core mode has no weight tiles
         with pytest.raises(pcal.PcalError):
             pcal.pcal_dft_weights_host(*args)
@@ -91,7 +96,7 @@ def test_weights_reject_bad_arguments(lib):
 
 def test_operand_split_matches_the_tile_layout(tmp_path):
     """The split kernel's per-thread words (its loop body run on the host)
-    equal the element-wise split of [Re P | Im P] into the tile layout, for
+    equal the element-wise split of [Re P | Im P] into each part's tile image, for
     ragged C and N and 8-byte-aligned P, and each mode's thread -> word map is
     a bijection on a tile (tests/host/dft_split_check.cu)."""
     nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"

@@ -1,13 +1,17 @@
 """Batched tone DFT (pcal_dft_*): CUDA-core FP32 and tensor-core (tcgen05) split-TF32 / split-BF16 modes
 against the DFT definition T_i = sum_b P[b] e^{-j 2 pi i b / N} in FP64 (numpy's FFT evaluates exactly that
-sum), with the error bound of each mode stated in the test."""
+sum), within the phasor tolerance of 1e-5 of the largest phasor; the tensor-core modes, whose chunk sums are
+added on CUDA cores in FP32, are held to the tighter bound of an FP32 sum."""
 import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu
 
-# max |T - T_ref| / max |T_ref| per channel (pcal.h states ~1e-7, ~1e-6, ~3e-5)
-BOUND = {"fp32": 1e-5, "tf32x3": 1e-5, "bf16x3": 2e-4}
+# max |T - T_ref| / max |T_ref| per channel: the phasor tolerance for the CUDA-core FP32 sums (sequential over
+# N terms, ~3e-6 measured at N = 1024); the tensor-core modes keep 2^-22 (split TF32) or 2^-26 (split BF16) of
+# each operand and add FP32 chunk sums rounded to nearest
+BOUND = {"fp32": 1e-5, "tf32x3": 2e-6, "bf16x6": 2e-6}
+MODES = ["fp32", "tf32x3", "bf16x6"]
 SHAPES = [(1, 16), (5, 50), (130, 64), (300, 256), (129, 1024), (64, 200)]
 
 
@@ -41,7 +45,7 @@ def rel_err(T, ref):
     return np.max(np.abs(T - ref), axis=1) / np.max(np.abs(ref), axis=1)
 
 
-@pytest.mark.parametrize("mode", ["fp32", "tf32x3", "bf16x3"])
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("shape", SHAPES, ids=[f"C{c}-N{n}" for c, n in SHAPES])
 def test_dft_matches_definition(pcal, mode, shape):
     C, N = shape
@@ -55,7 +59,7 @@ def test_dft_matches_definition(pcal, mode, shape):
     assert err.max() <= BOUND[mode], (mode, shape, err.max())
 
 
-@pytest.mark.parametrize("mode", ["fp32", "tf32x3", "bf16x3"])
+@pytest.mark.parametrize("mode", MODES)
 def test_pure_tone_closed_form(pcal, mode):
     """P[b] = e^{j 2 pi i0 b / N}: T = N at i0, 0 elsewhere."""
     N = 256
@@ -67,7 +71,7 @@ def test_pure_tone_closed_form(pcal, mode):
     assert rel_err(T, ref).max() <= BOUND[mode]
 
 
-@pytest.mark.parametrize("mode", ["tf32x3", "bf16x3"])
+@pytest.mark.parametrize("mode", ["tf32x3", "bf16x6"])
 def test_channel_result_does_not_depend_on_the_batch(pcal, mode):
     """Rows of the contraction are independent: a channel's tones are bit-identical alone and in a batch."""
     rng = np.random.default_rng(5)
