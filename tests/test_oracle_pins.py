@@ -321,6 +321,41 @@ def test_phase_residuals_chi_square_c1():
     assert 0.5 * dof < np.mean(stats) < 1.6 * dof, stats
 
 
+def test_sigma_td_matches_delay_scatter_over_seeds():
+    """sigma_td pinned by the statistics of the fit, not by its own formula.
+    Over n = 60 independent noise realisations of a config-1-shaped stream
+    (M a whole number of periods, so the tones and their images are
+    orthogonal), the fitted delays scatter with a sample variance s^2 whose
+    ratio (n-1) s^2 / sigma^2 follows chi^2 with n-1 degrees of freedom when
+    sigma is the true standard deviation of the estimator.  The reported
+    sigma_td (averaged over the seeds) must be that sigma: s / mean(sigma_td)
+    inside the two-sided 0.1 % chi^2 band, widened by the 2.5 % sampling
+    error of the mean.  It must also agree with the closed form for equal
+    tone weights, sigma_phi / (2 pi f_comb sqrt(N (N^2 - 1) / 12)) with
+    sigma_phi = sqrt(2/M)/A per tone in unit noise (Eq. 1 with phi_i =
+    2 pi f_i t_d: the slope's variance is sigma_phi^2 / sum (f_i - f_bar)^2),
+    and the delays must be unbiased.  A dropped 1/(N-2), a square root taken
+    twice or a missing 1/(2 pi) moves sigma_td by a factor of 3.7 or more."""
+    from scipy import stats as st
+
+    fs, fc, fo, amp, td, M = 16_000_000, 1_000_000, 10_000, 0.02, 3.7e-9, 1_600_000
+    N, n = fs // fc, 60
+    tds, sig = [], []
+    for seed in range(n):
+        x = synth.Stream(fs=fs, fc=fc, fo=fo, amp=amp, td=td, seed=31000 + seed).f32(0, M)
+        pr = oracle.products(oracle.fold(x, "f32", 0, fs, fc, fo), M, fs, fc, fo)
+        tds.append(pr["td"])
+        sig.append(pr["sigma_td"])
+    tds, sig = np.array(tds), np.array(sig)
+    s = np.std(tds, ddof=1)
+    lo, hi = np.sqrt(st.chi2.ppf([0.0005, 0.9995], n - 1) / (n - 1))
+    ratio = s / np.mean(sig)
+    assert 0.975 * lo < ratio < 1.025 * hi, (ratio, lo, hi)
+    closed = math.sqrt(2.0 / M) / amp / (2 * math.pi * fc * math.sqrt(N * (N * N - 1) / 12.0))
+    assert 0.88 < np.mean(sig) / closed < 1.08, np.mean(sig) / closed
+    assert abs(np.mean(tds) - td) < 4 * closed / math.sqrt(n)
+
+
 # ---------------------------------------------------------- planted mistakes
 
 def _pin_battery():
