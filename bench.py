@@ -499,13 +499,21 @@ def run_gpu(args):
                                              ("value", "unit", "ms_per_step", "plain", "graph", "roofline", "config"))
             torch.cuda.empty_cache()
             out["serving"] = summarize_extra(lambda: run_serve(extra_args(args), emit=False),
-                                             ("p50_ms", "p99_ms", "periods", "realtime", "saturation", "config"))
+                                             ("p50_ms", "p99_ms", "periods", "lag", "realtime", "saturation", "config"))
             torch.cuda.empty_cache()
             out["tensor_dft"] = summarize_extra(lambda: run_tensor_dft(extra_args(args), emit=False),
                                                 ("modes", "speedup_vs_fp32", "config"))
             torch.cuda.empty_cache()
             out["c1_f32"] = summarize_extra(lambda: run_c1(extra_args(args), emit=False),
-                                            ("value", "unit", "ms_per_step", "roofline", "config"))
+                                            ("value", "unit", "ms_per_step", "step_frac", "roofline", "config"))
+            torch.cuda.empty_cache()
+            out["precision"] = summarize_extra(lambda: run_precision(extra_args(args), emit=False),
+                                               ("value", "unit", "variants", "config"))
+            torch.cuda.empty_cache()
+            out["rotplan"] = summarize_extra(lambda: run_rotplan(extra_args(args), emit=False),
+                                             ("value", "unit", "ms_per_step", "prefix_max_phasor_err_rel", "config"))
+            # the driver keeps the end of the line: the metric's parts, compact, come last
+            out["summary"] = compact_summary(out)
         print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
@@ -727,7 +735,7 @@ def run_batch(args, emit=True):
                          f"({dt:.1f} s)"}
     # the finalize alone with each tone DFT (fused CUDA-core FP32 vs one tensor-core contraction per N)
     fin_modes = {}
-    for mode in ("fp32", "tf32x3", "bf16x3"):
+    for mode in ("fp32", "tf32x3", "bf16x6"):
         batch.set_dft(mode)
         batch.accumulate(ptrs, n, stream)
         for _ in range(3):
@@ -820,6 +828,7 @@ def run_c1(args, emit=True, n_buffers=8):
     nbytes = 4 * m
     out = {"metric": "PCal Gsamples/s (f32 single-stream extraction: accumulate + finalize)",
            "value": m / (step_ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": step_ms, "steps": k,
+           "step_frac": nbytes / (step_ms / 1e3) / 1e9 / peak,
            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
            "config": {"workload": C1_WORKLOAD, "fold_ms": fold_ms, "td_s": res["td"], "sigma_td_s": res["sigma_td"],
                       "l2": f"inputs rotate over {n_buffers} device buffers ({n_buffers * nbytes >> 20} MB) > L2"},
@@ -855,7 +864,8 @@ def run_tensor_dft(args, emit=True, C=4096, N=1024, reps=20):
     dT = torch.empty((C, N), dtype=torch.complex64, device="cuda")
     peak_bf16, peak_kind = read_tensor_peak()
     modes = {}
-    for mode in ("fp32", "tf32x3", "bf16x3"):
+    method_flops = 8.0 * C * N * N  # the DFT itself: C x N x N complex multiply-adds
+    for mode in ("fp32", "tf32x3", "bf16x6"):
         with pcal.Dft(N, mode) as d:
             for _ in range(3):
                 d.execute(dP, C, dT)
@@ -869,22 +879,25 @@ def run_tensor_dft(args, emit=True, C=4096, N=1024, reps=20):
             flags = d.check()
         T = dT.cpu().numpy()
         err = np.max(np.abs(T - ref), axis=1) / np.max(np.abs(ref), axis=1)
-        if mode == "fp32":
-            flops = 8.0 * C * N * N  # complex MACs on CUDA cores
-            roof = None
-        else:
-            flops = 3 * 2.0 * C * (2 * N) * (2 * N)  # three real C x 2N x 2N products
+        roof = None
+        executed = method_flops
+        if mode != "fp32":
+            # real C x 2N x 2N products: three (split TF32) or six (split BF16)
+            executed = (3 if mode == "tf32x3" else 6) * 2.0 * C * (2 * N) * (2 * N)
             # TF32 from the measured bf16 peak and the nominal dense ratio (1.1 / 2.25 PFLOP/s)
             peak = peak_bf16 * (1.1 / 2.25) if mode == "tf32x3" else peak_bf16
-            ach = flops / (ms / 1e3) / 1e12
+            ach = method_flops / (ms / 1e3) / 1e12
             roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                    "traffic": None, "peak_kind": f"{peak_kind} bf16 burst" + (" x 1.1/2.25 (tf32)" if mode == "tf32x3" else "")}
-        modes[mode] = {"ms": ms, "tflops": flops / (ms / 1e3) / 1e12, "max_rel_err": float(err.max()),
+                    "traffic": None, "work": "method flops 8 C N^2 (the DFT itself)",
+                    "executed_tflops": executed / (ms / 1e3) / 1e12,
+                    "executed_frac": executed / (ms / 1e3) / 1e12 / peak,
+                    "peak_kind": f"{peak_kind} bf16 burst" + (" x 1.1/2.25 (tf32)" if mode == "tf32x3" else "")}
+        modes[mode] = {"ms": ms, "tflops": method_flops / (ms / 1e3) / 1e12, "max_rel_err": float(err.max()),
                        "median_rel_err": float(np.median(err)), "device_error_bits": flags, "roofline": roof}
-    out = {"metric": "batched tone DFT time per launch", "value": modes["bf16x3"]["ms"], "unit": "ms",
+    out = {"metric": "batched tone DFT time per launch", "value": modes["tf32x3"]["ms"], "unit": "ms",
            "higher_is_better": False, "data": "synthetic", "config": {"workload": DFT_WORKLOAD, "C": C, "N": N},
            "modes": modes,
-           "speedup_vs_fp32": {m: modes["fp32"]["ms"] / modes[m]["ms"] for m in ("tf32x3", "bf16x3")}}
+           "speedup_vs_fp32": {m: modes["fp32"]["ms"] / modes[m]["ms"] for m in ("tf32x3", "bf16x6")}}
     if emit:
         print(json.dumps(out))
     return out
@@ -948,15 +961,21 @@ def run_serve(args, emit=True):
     srv = pcal.Server(args.serve_budget_gb << 30, len(streams), period_s, 0.1)
     ids = [srv.open(st["fs"], st["fc"], st["fo"], st["fmt"]) for st in streams]
     rng = np.random.default_rng(SERVE_SEED + 1)
+    t_adm = time.perf_counter()  # every stream admitted (its memory carved) before the clock starts
+    while srv.stats()["admitted"] < len(streams) and time.perf_counter() - t_adm < 30:
+        time.sleep(0.001)
 
-    # real time: each stream's chunks arrive as a Poisson process (mean chunk_s);
-    # due chunks are submitted together every tick
+    # real time: each stream's chunks arrive as a Poisson process (mean chunk_s); due chunks are submitted
+    # together every tick, each stamped with its scheduled arrival time, so a period's latency runs from
+    # the arrival of its last chunk (through any submit lag, the copy, the fold and the finalize) to its
+    # results on the host
     clocks = ClockSampler(dev)
     clocks.start()
     t0 = time.perf_counter()
+    lib0 = pcal.clock_s() - (time.perf_counter() - t0)  # library clock at t0
     next_t = t0 + rng.exponential(chunk_s, len(streams))
     sent = np.zeros(len(streams), dtype=np.int64)
-    lag_max = 0.0
+    lags = []
     duration = args.serve_seconds
     while True:
         now = time.perf_counter()
@@ -966,9 +985,10 @@ def run_serve(args, emit=True):
         if due.size == 0:
             time.sleep(max(0.0, min(next_t.min() - now, 0.001)))
             continue
-        lag_max = max(lag_max, float(now - next_t[due].min()))
+        arrivals = next_t[due]
+        lags.extend((now - arrivals).tolist())
         srv.submit_many([ids[i] for i in due], [pools[i][sent[i] % 2][1] for i in due],
-                        [pools[i][sent[i] % 2][2] for i in due])
+                        [pools[i][sent[i] % 2][2] for i in due], arrival_s=(lib0 + (arrivals - t0)).tolist())
         sent[due] += 1
         next_t[due] += rng.exponential(chunk_s, due.size)
     t_rt = time.perf_counter() - t0
@@ -982,6 +1002,7 @@ def run_serve(args, emit=True):
             break
         lat.append(r["latency_s"])
     rt_samples = int(sum(sent[i] * pools[i][0][2] for i in range(len(streams))))
+    lags.sort()
 
     # saturation: every stream submits its next second of chunks as fast as the
     # rings and the GPU take them
@@ -1002,15 +1023,20 @@ def run_serve(args, emit=True):
     p99 = lat[int((len(lat) - 1) * 0.99)] if lat else None
     if rank == 0:
         out = {
-            "metric": "PCal serving p99 latency (last chunk of a 1 s period submitted -> phasors on the host)",
+            "metric": "PCal serving p99 latency (arrival of the last chunk of a 1 s period -> phasors on the host)",
             "value": p99 * 1e3 if p99 is not None else None, "unit": "ms", "n_gpus": world, "steps": len(lat),
             "warmup": 0, "ms_per_step": None, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "u32", "data": "synthetic",
             "config": {"workload": SERVE_WORKLOAD, "streams": len(streams), "offered_GBps": rate / 1e9,
-                       "realtime_seconds": t_rt, "max_submit_lag_s": lag_max, "hbm_budget_GB": args.serve_budget_gb,
+                       "realtime_seconds": t_rt, "hbm_budget_GB": args.serve_budget_gb,
+                       "latency": "scheduled arrival of a period's last chunk -> phasors on the host",
                        "chunk_pool": "2 distinct seeded chunks per stream, repeated"},
             "p50_ms": p50 * 1e3 if p50 is not None else None, "p99_ms": p99 * 1e3 if p99 is not None else None,
             "periods": len(lat),
+            "lag": {"p50_ms": lags[(len(lags) - 1) // 2] * 1e3 if lags else None,
+                    "p99_ms": lags[int((len(lags) - 1) * 0.99)] * 1e3 if lags else None,
+                    "max_ms": lags[-1] * 1e3 if lags else None, "chunks": len(lags),
+                    "what": "scheduled arrival -> submit start"},
             "realtime": {"value": rt_samples / t_rt / 1e9, "unit": UNIT, "launches": rt["launches"],
                          "admitted": rt["admitted"], "hbm_in_use_GB": rt["hbm_in_use"] / 2**30},
             "saturation": {"value": sat_samples / t_sat / 1e9, "unit": UNIT, "h2d_GBps": sat_bytes / t_sat / 1e9,
@@ -1029,10 +1055,15 @@ def run_serve(args, emit=True):
 
 PREC_SEED = 2501059932 + 2
 PREC_WORKLOAD = ("int8 (sigma 20), fs 1024 MHz, f_comb 1 MHz (N 1024), f_offset 10 kHz (L 102400), 16.384e9 "
-                 "samples (16 s) streamed in 2^30-sample chunks (not L-aligned), tone amplitude 1e-3 sigma")
+                 "samples (16 s) streamed in 2^30-sample chunks (not L-aligned), tone amplitude 1e-3 sigma; the "
+                 "stream repeats one seeded block of 256 periods L (26.2M samples), so the comb stays coherent")
+PREC_BLOCK_PERIODS = 256
 
 
-def run_precision(args):
+def run_precision(args, emit=True):
+    """C4: every accumulation variant over the same 16.4G int8 samples, phase error per tone against the
+    FP64 oracle's exact bins.  The stream is one seeded block of whole periods repeated, so the oracle's
+    bins are (repeats) x (the block's bins) + (the bins of the last partial block), exactly."""
     import torch
 
     import oracle
@@ -1046,12 +1077,18 @@ def run_precision(args):
     fs, fc, fo, N = 1_024_000_000, 1_000_000, 10_000, 1024
     total = int(16.384e9 * args.prec_scale) // 4 * 4
     chunk = 1 << 30
-    stream = synth.Stream(fs=fs, fc=fc, fo=fo, amp=1e-3, td=12.5e-9, seed=PREC_SEED)
     plan_i8 = pcal.Plan(fs, fc, fo, "i8")
     plan_f32 = pcal.Plan(fs, fc, fo, "f32")
     rot = {v: pcal.RotFold(fs, fc, fo, "i8", v, lanes=args.prec_lanes) for v in ("table", "table_kahan", "dfr")}
     L = plan_i8.L
-    S = np.zeros(L, dtype=np.int64)  # the oracle's exact bins
+    B = L * PREC_BLOCK_PERIODS
+    block = synth.Stream(fs=fs, fc=fc, fo=fo, amp=1e-3, td=12.5e-9, seed=PREC_SEED).samples("i8", 0, B)
+    q, r = divmod(total, B)
+    S = q * oracle.sums_i8(block, 0, L) + oracle.sums_i8(block[:r], 0, L)  # the oracle's exact bins
+    dblk = torch.from_numpy(block).cuda()
+    reps = (min(chunk, total) + B - 1) // B + 1
+    R = dblk.repeat(reps)  # R[j] = block[j mod B] for every window of one chunk
+    del dblk
     times = {k: 0.0 for k in ("fold-first int64", "fold-first fp32 compensated", "table", "table_kahan", "dfr")}
     s_ev, e_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     cur = torch.cuda.current_stream()
@@ -1066,24 +1103,24 @@ def run_precision(args):
     n0 = 0
     while n0 < total:
         n = min(chunk, total - n0)
-        host = stream.samples("i8", n0, n)
-        d = torch.from_numpy(host).cuda()
+        o = n0 % B
+        d = R[o:o + n]
         timed("fold-first int64", lambda: plan_i8.accumulate(d, n))
         df32 = d.float()
         timed("fold-first fp32 compensated", lambda: plan_f32.accumulate(df32, n))
         del df32
-        for v, r in rot.items():
-            timed(v, lambda r=r: r.accumulate(d, n))
-        S += oracle.sums_i8(host, n0, L)
+        for v, rf in rot.items():
+            timed(v, lambda rf=rf: rf.accumulate(d, n))
         n0 += n
-        del d
+    del R
     ref = oracle.tones_from_bins(S.astype(np.float64), fs, fc, fo)
     results = {"fold-first int64": plan_i8.finalize(), "fold-first fp32 compensated": plan_f32.finalize()}
-    for v, r in rot.items():
-        results[v] = r.finalize()
-        r.close()
+    for v, rf in rot.items():
+        results[v] = rf.finalize()
+        rf.close()
     plan_i8.close()
     plan_f32.close()
+    torch.cuda.empty_cache()
     scale = float(np.max(np.abs(ref)))
     sig = np.abs(ref) > 1e-3 * scale
     variants = {}
@@ -1101,7 +1138,121 @@ def run_precision(args):
                    "tones_compared": int(sig.sum())},
         "variants": variants,
     }
-    print(json.dumps(out))
+    if emit:
+        print(json.dumps(out))
+    return out
+
+
+# ---- long-period plan: a prime comb offset, every sample rotated ----------------------------
+
+ROT_WORKLOAD = ("int8 (sigma 20), fs 64 MHz, f_comb 1 MHz (N 64), f_offset 10007 Hz (prime: period 64e6 samples, "
+                "no fold), 256M samples (4 s) per step, tone amplitude 0.01 sigma")
+
+
+def run_rotplan(args, emit=True, m=256 << 20, k_steps=5):
+    """Long-period plan throughput (accumulate + finalize per step, inputs rotating over two device buffers
+    of 256 MB), and its phasors on a 4M-sample prefix against the oracle's direct definition."""
+    import torch
+
+    import oracle
+    import paper_2501_05993_gb300 as pcal
+    import synth
+    from paper_2501_05993_gb300 import build as libbuild
+
+    torch.cuda.set_device(0)
+    libbuild.build()
+    pcal.load()
+    fs, fc, fo = 64_000_000, 1_000_000, 10_007.0
+    s = synth.Stream(fs=fs, fc=fc, fo=fo, amp=0.01, td=12.5e-9, seed=2501059932 + 7)
+    pre = 4_000_000
+    head = s.samples("i8", 0, pre)
+    with pcal.RotPlan(fs, fc, fo, "i8") as rp:
+        rp.accumulate(torch.from_numpy(head).cuda(), pre)
+        rp.finalize_device()
+        T = rp.results()["phasors"]
+    ref = oracle.direct_any(head, "i8", 0, fs, fc, fo)
+    err = float(np.max(np.abs(T - ref)) / np.max(np.abs(ref)))
+    base = torch.from_numpy(head).cuda()
+    bufs = [base.repeat(m // pre + 1)[:m].contiguous() for _ in range(2)]
+    stream = torch.cuda.current_stream()
+    with pcal.RotPlan(fs, fc, fo, "i8") as rp:
+        for i in range(2):
+            rp.accumulate(bufs[i % 2], m, stream)
+            rp.finalize_device(stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(k_steps):
+            rp.accumulate(bufs[i % 2], m, stream)
+            rp.finalize_device(stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / k_steps
+    del bufs, base
+    torch.cuda.empty_cache()
+    out = {"metric": "PCal Gsamples/s, long-period plan (per-sample rotation)", "value": m / (ms / 1e3) / 1e9,
+           "unit": UNIT, "ms_per_step": ms, "steps": k_steps, "higher_is_better": True, "dtype": "f32 (double-float)",
+           "data": "synthetic", "config": {"workload": ROT_WORKLOAD, "samples_per_step": m},
+           "prefix_max_phasor_err_rel": err}
+    if emit:
+        print(json.dumps(out))
+    return out
+
+
+def _sig(x, digits=4):
+    """x rounded to `digits` significant digits (None and non-numbers pass through)."""
+    if isinstance(x, bool) or not isinstance(x, (int, float)) or x == 0 or x != x:
+        return x
+    from math import floor, log10
+
+    return round(float(x), -int(floor(log10(abs(x)))) + digits - 1)
+
+
+def compact_summary(out: dict) -> dict:
+    """The headline metric's parts in a few hundred characters, written last on the line."""
+
+    def get(d, *path):
+        for k in path:
+            if not isinstance(d, dict):
+                return None
+            d = d.get(k)
+        return d
+
+    sm = {"c2": {"gs": _sig(out.get("value")), "step_us": _sig(out.get("ms_per_step", 0) * 1e3),
+                 "fold_frac": _sig(get(out, "roofline", "frac"), 3), "e2e_gs": _sig(get(out, "e2e", "value"))}}
+    c1 = out.get("c1_f32") or {}
+    if "value" in c1:
+        sm["c1_f32"] = {"gs": _sig(c1["value"]), "step_frac": _sig(c1.get("step_frac"), 3),
+                        "fold_frac": _sig(get(c1, "roofline", "frac"), 3)}
+    b = out.get("batched") or {}
+    if "value" in b:
+        pv = get(b, "plain", "value")
+        sm["batched"] = {"gs": _sig(b["value"]), "plain_gs": _sig(pv), "graph_gs": _sig(get(b, "graph", "value")),
+                         "x_plain": _sig(b["value"] / pv, 3) if pv else None,
+                         "fold_frac": _sig(get(b, "roofline", "frac"), 3),
+                         "e2e_gs": _sig(get(b, "e2e", "value")),
+                         "phasor_diff": _sig(get(b, "config", "batched_vs_plain_max_phasor_diff"), 2)}
+    sv = out.get("serving") or {}
+    if "p99_ms" in sv:
+        sm["serving"] = {"p50_ms": _sig(sv["p50_ms"], 3), "p99_ms": _sig(sv["p99_ms"], 3),
+                         "lag_p99_ms": _sig(get(sv, "lag", "p99_ms"), 3), "lag_max_ms": _sig(get(sv, "lag", "max_ms"), 3),
+                         "rt_gs": _sig(get(sv, "realtime", "value"), 3), "sat_gs": _sig(get(sv, "saturation", "value"), 3),
+                         "periods": sv.get("periods")}
+    pr = out.get("precision") or {}
+    if "variants" in pr:
+        short = {"fold-first int64": "int64", "fold-first fp32 compensated": "f32c", "table": "tab",
+                 "table_kahan": "tab_kahan", "dfr": "dfr"}
+        sm["precision"] = {short[k]: [_sig(v["gsamples_per_s"], 3), _sig(v["max_phase_err_rad"], 2)]
+                           for k, v in pr["variants"].items()}
+        sm["precision"]["fmt"] = "[Gs/s, max phase err rad]"
+    rp = out.get("rotplan") or {}
+    if "value" in rp:
+        sm["rotplan"] = {"gs": _sig(rp["value"], 3), "err": _sig(rp.get("prefix_max_phasor_err_rel"), 2)}
+    td = get(out, "tensor_dft", "modes") or {}
+    if td:
+        sm["dft"] = {m: [_sig(v["ms"], 3), _sig(v["max_rel_err"], 2), _sig(get(v, "roofline", "frac"), 3)]
+                     for m, v in td.items()}
+        sm["dft"]["fmt"] = "[ms, max err, method-work frac]"
+    return sm
 
 
 def main():
@@ -1124,7 +1275,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="single workload: skip the batched and serving summaries")
     ap.add_argument("--prec-scale", type=float, default=1.0, help="precision workload: fraction of the 16 s")
     ap.add_argument("--prec-lanes", type=int, default=128)
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "precision", "dft", "c1"],
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "precision", "dft", "c1", "rotplan"],
                     help="single: the 2-bit single-channel headline workload; batch: 64 mixed channels")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -1137,6 +1288,8 @@ def main():
         run_serve(args)
     elif args.workload == "precision":
         run_precision(args)
+    elif args.workload == "rotplan":
+        run_rotplan(args)
     elif args.workload == "dft":
         run_tensor_dft(args)
     elif args.workload == "c1":

@@ -187,3 +187,30 @@ def test_serve_rejects_bad_streams(pcal):
         srv.drain(10)
         with pytest.raises(pcal.PcalError):
             srv.submit(sid, np.zeros(16, np.uint8), 64)
+
+
+def test_serve_latency_counts_from_the_chunk_arrival(pcal):
+    """A period's latency runs from the arrival the client stamps on the chunk
+    that completes it to its results on the host: a chunk stamped as having
+    arrived 0.25 s before its submit reports at least 0.25 s more than the
+    same chunk stamped at its submit, and an unstamped chunk counts from the
+    submit's return."""
+    st = STREAMS[0]
+    host = stream_samples(0, st, 3)
+    parts = chunks(host, st)
+    per = len(parts) // 3
+    with pcal.Server(1 << 30, 4, PERIOD_S, RING_S) as srv:
+        sid = srv.open(*st)
+        lat = []
+        for period, lag in enumerate((0.25, 0.0, None)):
+            for k, (_, arr, n) in enumerate(parts[period * per:(period + 1) * per]):
+                when = None if lag is None else [pcal.clock_s() - (lag if k == per - 1 else 0.0)]
+                srv.submit_many([sid], [arr], [n], arrival_s=when)
+            srv.drain(30)
+            r = srv.poll(5.0)
+            assert r is not None and r["period"] == period
+            lat.append(r["latency_s"])
+        with pytest.raises(pcal.PcalError):
+            srv.submit_many([sid], [parts[0][1]], [parts[0][2]], arrival_s=[float("nan")])
+    assert lat[0] >= 0.25 + lat[1] - 0.05 and lat[0] >= 0.25
+    assert 0 < lat[1] < 0.2 and 0 < lat[2] < 0.2
