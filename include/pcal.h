@@ -315,7 +315,14 @@ typedef struct {
     int sample_format;           /* PCAL_2BIT or PCAL_I8                      */
 } pcal_channel_desc;
 
-/* Launch schedule of the persistent fold (pcal_batch_autotune picks one). */
+/* Launch schedule of the persistent fold (pcal_batch_autotune picks one).
+ * A channel's tile is a column group of its rows (one row = a whole number of
+ * periods L); its width is capped by the channel's bucket -- sample format x
+ * row width -- or, where the bucket's cap is 0, by col_cap.  Bucket index =
+ * 4 * (format == PCAL_I8) + class, class 0: rows of at most 256 32-bit
+ * words, 1: at most 1024, 2: at most 4096, 3: wider.  box_rows, stages and
+ * ctas shape the one launch, so they are per batch. */
+#define PCAL_SCHED_BUCKETS 8
 typedef struct {
     int ctas;        /* CTAs of the fold launch; 0 = one per SM                */
     int box_rows;    /* rows per TMA box: 32 or 64                              */
@@ -323,6 +330,7 @@ typedef struct {
     int static_pct;  /* percent of the boxes handed out statically (0..100)     */
     int min_chunk;   /* smallest dynamic grab, boxes (1..4096)                  */
     int col_cap;     /* widest column group, 32-bit words: 128 or 224           */
+    int col_cap_bucket[PCAL_SCHED_BUCKETS]; /* per bucket: 0 (= col_cap), 64, 128 or 224 */
 } pcal_schedule;
 
 typedef struct pcal_batch pcal_batch;
@@ -346,6 +354,9 @@ int pcal_batch_set_schedule(pcal_batch* batch, const pcal_schedule* sched);
  * Synchronises the device; drops captured step graphs. */
 int pcal_batch_set_dft(pcal_batch* batch, int mode);
 int pcal_batch_get_schedule(const pcal_batch* batch, pcal_schedule* out);
+/* The tile a channel's rows are cut into under the current schedule (host only): its bucket (the
+ * index into col_cap_bucket), the column-group width in 32-bit words and the number of groups. */
+int pcal_batch_channel_tiling(const pcal_batch* batch, int channel, int* bucket, int* col_width, int* col_groups);
 
 /*
  * Fold n[c] more samples of every channel c.  samples: HOST array of
@@ -391,11 +402,14 @@ int pcal_batch_get_bins(pcal_batch* batch, int channel, int64_t* host_out);
 int pcal_batch_get_stats(const pcal_batch* batch, pcal_stats* out);
 
 /*
- * Time candidate schedules (column-width cap, box rows, static share, chunk
- * size) on these inputs, accumulate only, and keep the fastest; writes it to
- * *chosen when not NULL.  The batch must be at a period boundary (PCAL_EBUSY
- * otherwise); its bins are emptied and its indices restored afterwards.
- * Synchronous.
+ * Time candidate schedules on these inputs, accumulate only, and keep the
+ * fastest; writes it to *chosen when not NULL.  Three passes: the batch-wide
+ * choices (column-width cap, box rows, static share, chunk size; the four
+ * fastest timed again), then the CTA count (one per SM, or 8 or 16 fewer),
+ * then, one bucket at a time for the buckets the batch's channels occupy, the
+ * bucket's own column-width cap (64, 128, 224), each kept only when it is
+ * faster.  The batch must be at a period boundary (PCAL_EBUSY otherwise); its
+ * bins are emptied and its indices restored afterwards.  Synchronous.
  */
 int pcal_batch_autotune(pcal_batch* batch, const void* const* samples, const int64_t* n, void* stream,
                         pcal_schedule* chosen);

@@ -59,12 +59,16 @@ class ChannelDesc(ctypes.Structure):
                 ("N", ctypes.c_int), ("sample_format", ctypes.c_int)]
 
 
+PCAL_SCHED_BUCKETS = 8
+
+
 class Schedule(ctypes.Structure):
     _fields_ = [("ctas", ctypes.c_int), ("box_rows", ctypes.c_int), ("stages", ctypes.c_int),
-                ("static_pct", ctypes.c_int), ("min_chunk", ctypes.c_int), ("col_cap", ctypes.c_int)]
+                ("static_pct", ctypes.c_int), ("min_chunk", ctypes.c_int), ("col_cap", ctypes.c_int),
+                ("col_cap_bucket", ctypes.c_int * PCAL_SCHED_BUCKETS)]
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        return {k: (list(getattr(self, k)) if k == "col_cap_bucket" else getattr(self, k)) for k, _ in self._fields_}
 
 
 PCAL_MAX_BATCH, PCAL_BATCH_MAX_N = 4096, 1024
@@ -139,6 +143,7 @@ def load(path: str | None = None):
         "pcal_batch_get_geometry": ([vp, ci, P(Geometry)], ci),
         "pcal_batch_set_schedule": ([vp, P(Schedule)], ci),
         "pcal_batch_get_schedule": ([vp, P(Schedule)], ci),
+        "pcal_batch_channel_tiling": ([vp, ci, P(ci), P(ci), P(ci)], ci),
         "pcal_batch_accumulate": ([vp, P(vp), P(i64), vp], ci),
         "pcal_batch_finalize_device": ([vp, vp], ci),
         "pcal_batch_step_graph": ([vp, P(vp), P(i64), vp], ci),
@@ -636,8 +641,21 @@ class Batch:
     def set_schedule(self, **kw):
         s = pcal_batch_get_schedule(self.handle)
         for k, v in kw.items():
-            setattr(s, k, int(v))
+            if k == "col_cap_bucket":
+                if len(v) != PCAL_SCHED_BUCKETS:
+                    raise ValueError(f"col_cap_bucket takes {PCAL_SCHED_BUCKETS} caps")
+                for i, x in enumerate(v):
+                    s.col_cap_bucket[i] = int(x)
+            else:
+                setattr(s, k, int(v))
         pcal_batch_set_schedule(self.handle, s)
+
+    def channel_tiling(self, channel: int) -> dict:
+        """The bucket, column-group width (32-bit words) and group count of a channel's rows."""
+        bk, cw, gc = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(load().pcal_batch_channel_tiling(self.handle, int(channel), ctypes.byref(bk), ctypes.byref(cw),
+                                                ctypes.byref(gc)), "pcal_batch_channel_tiling")
+        return {"bucket": bk.value, "col_width": cw.value, "col_groups": gc.value}
 
     def set_dft(self, mode: str):
         """Tone DFT of the finalize: "fp32" (inside each channel's cluster), "tf32x3" or "bf16x6"

@@ -686,7 +686,28 @@ cudaError_t batch_launch_tables(BatchChan& C, const pcal_geometry& g, cudaStream
 }
 
 // Fill the constant part of a channel's device record (pointers excluded).
-void batch_fill_chan(BatchChan& C, const pcal_geometry& g, double f_comb, int col_cap) {
+int sched_bucket(int fmt, int cols_total) {
+    const int cls = cols_total <= 256 ? 0 : cols_total <= 1024 ? 1 : cols_total <= 4096 ? 2 : 3;
+    return (fmt == PCAL_I8 ? 4 : 0) + cls;
+}
+
+int chan_col_cap(const pcal_schedule& sc, int fmt, int cols_total) {
+    const int b = sc.col_cap_bucket[sched_bucket(fmt, cols_total)];
+    return b > 0 ? b : sc.col_cap;
+}
+
+// Column groups of a channel's rows for a width cap: as few groups as the cap
+// allows, of equal width rounded up to 8 words.
+void chan_cut(BatchChan& C, int cap) {
+    int gc = (C.cols_total + cap - 1) / cap;
+    int cw = (C.cols_total + gc - 1) / gc;
+    cw = (cw + 7) / 8 * 8;
+    if (cw > cap) cw = cap;
+    C.col_groups = (C.cols_total + cw - 1) / cw;
+    C.col_width = cw;
+}
+
+void batch_fill_chan(BatchChan& C, const pcal_geometry& g, double f_comb, const pcal_schedule& sc) {
     memset(static_cast<void*>(&C), 0, sizeof(C));
     C.fmt = g.format;
     C.spw = g.samples_per_byte_x4;
@@ -695,12 +716,7 @@ void batch_fill_chan(BatchChan& C, const pcal_geometry& g, double f_comb, int co
     C.so = g.step_offset;
     C.row_samples = g.row_samples;
     C.cols_total = (int)(g.row_samples / C.spw);
-    int gc = (C.cols_total + col_cap - 1) / col_cap;
-    int cw = (C.cols_total + gc - 1) / gc;
-    cw = (cw + 7) / 8 * 8;
-    if (cw > col_cap) cw = col_cap;
-    C.col_groups = (C.cols_total + cw - 1) / cw;
-    C.col_width = cw;
+    chan_cut(C, chan_col_cap(sc, C.fmt, C.cols_total));
     const double lv[4] = {-3.3359, -1.0, 1.0, 3.3359};
     C.lev0 = g.format == PCAL_2BIT ? lv[0] : 0.0;
     C.c_l = g.format == PCAL_2BIT ? lv[1] - lv[0] : 0.0;
@@ -745,19 +761,21 @@ namespace {
 
 int shape_for(const pcal_batch* b, BatchShape* s) { return batch_shape(b->sched, b->cw_max, b->num_sms, s); }
 
-// Column groups of every channel for a column-width cap (the rule of
+// Column groups of every channel under a schedule's caps (the rule of
 // batch_fill_chan), and the widest group.
-void apply_col_cap(pcal_batch* b, int cap) {
+void apply_col_caps(pcal_batch* b, const pcal_schedule& sc) {
     b->cw_max = 8;
     for (BatchChan& C : b->h_ch) {
-        int gc = (C.cols_total + cap - 1) / cap;
-        int cw = (C.cols_total + gc - 1) / gc;
-        cw = (cw + 7) / 8 * 8;
-        if (cw > cap) cw = cap;
-        C.col_width = cw;
-        C.col_groups = (C.cols_total + cw - 1) / cw;
-        if (cw > b->cw_max) b->cw_max = cw;
+        chan_cut(C, chan_col_cap(sc, C.fmt, C.cols_total));
+        if (C.col_width > b->cw_max) b->cw_max = C.col_width;
     }
+}
+
+bool same_caps(const pcal_schedule& x, const pcal_schedule& y) {
+    if (x.col_cap != y.col_cap) return false;
+    for (int i = 0; i < PCAL_SCHED_BUCKETS; ++i)
+        if (x.col_cap_bucket[i] != y.col_cap_bucket[i]) return false;
+    return true;
 }
 
 int build_call(pcal_batch* b, const void* const* samples, const int64_t* n, const BatchShape& sh,
@@ -789,7 +807,7 @@ extern "C" int pcal_batch_create(const pcal_channel_desc* channels, int n_channe
     b->h_ch.resize(n_channels);
     b->n_abs.assign(n_channels, 0);
     b->period_start.assign(n_channels, 0);
-    b->sched = pcal_schedule{0, 32, 0, 90, 4, 224};
+    b->sched = pcal_schedule{0, 32, 0, 90, 4, 224, {}};
     size_t pool = 0;
     std::vector<size_t> off(n_channels);
     for (int c = 0; c < n_channels; ++c) {
@@ -824,7 +842,7 @@ extern "C" int pcal_batch_create(const pcal_channel_desc* channels, int n_channe
     b->max_n = 1;
     for (int c = 0; c < n_channels && e == cudaSuccess; ++c) {
         BatchChan& C = b->h_ch[c];
-        batch_fill_chan(C, b->g[c], channels[c].f_comb, b->sched.col_cap);
+        batch_fill_chan(C, b->g[c], channels[c].f_comb, b->sched);
         batch_place_chan(C, b->g[c], base + off[c]);
         if (C.col_width > b->cw_max) b->cw_max = C.col_width;
         if (C.N > b->max_n) b->max_n = C.N;
@@ -987,15 +1005,29 @@ extern "C" int pcal_batch_set_schedule(pcal_batch* b, const pcal_schedule* s) {
         s->stages > 8 || s->static_pct < 0 || s->static_pct > 100 || s->min_chunk < 1 || s->min_chunk > 4096 ||
         (s->col_cap != 128 && s->col_cap != 224))
         return PCAL_EINVAL;
+    for (int i = 0; i < PCAL_SCHED_BUCKETS; ++i) {
+        const int v = s->col_cap_bucket[i];
+        if (v != 0 && v != 64 && v != 128 && v != 224) return PCAL_EINVAL;
+    }
     const pcal_schedule old = b->sched;
     b->sched = *s;
-    if (s->col_cap != old.col_cap) apply_col_cap(b, s->col_cap);
+    if (!same_caps(*s, old)) apply_col_caps(b, *s);
     BatchShape sh;
     if (shape_for(b, &sh) != 0) {
         b->sched = old;
-        apply_col_cap(b, old.col_cap);
+        apply_col_caps(b, old);
         return PCAL_EINVAL;
     }
+    return PCAL_OK;
+}
+
+extern "C" int pcal_batch_channel_tiling(const pcal_batch* b, int channel, int* bucket, int* col_width,
+                                         int* col_groups) {
+    if (!b || channel < 0 || channel >= b->n || !bucket || !col_width || !col_groups) return PCAL_EINVAL;
+    const BatchChan& C = b->h_ch[channel];
+    *bucket = sched_bucket(C.fmt, C.cols_total);
+    *col_width = C.col_width;
+    *col_groups = C.col_groups;
     return PCAL_OK;
 }
 
@@ -1228,7 +1260,7 @@ extern "C" int pcal_batch_autotune(pcal_batch* b, const void* const* samples, co
     for (int cap : {224, 128})
         for (int rows : {32, 64})
             for (int pct : {85, 95})
-                for (int chunk : {8, 32, 64, 128}) cand.push_back(pcal_schedule{0, rows, 0, pct, chunk, cap});
+                for (int chunk : {8, 32, 64, 128}) cand.push_back(pcal_schedule{0, rows, 0, pct, chunk, cap, {}});
     const pcal_schedule keep = b->sched;
     const int cw_keep = b->cw_max;
     const std::vector<BatchChan> ch_keep = b->h_ch;
@@ -1239,7 +1271,7 @@ extern "C" int pcal_batch_autotune(pcal_batch* b, const void* const* samples, co
     // time one candidate: `reps` accumulates after one that warms up (ms per accumulate, or < 0)
     auto time_cand = [&](const pcal_schedule& cs, int reps) -> float {
         b->sched = cs;
-        apply_col_cap(b, cs.col_cap);
+        apply_col_caps(b, cs);
         BatchShape sh;
         if (shape_for(b, &sh) != 0) return -1.f;
         float ms = 0.f;
@@ -1254,7 +1286,7 @@ extern "C" int pcal_batch_autotune(pcal_batch* b, const void* const* samples, co
         }
         return rc == PCAL_OK ? ms / reps : -1.f;
     };
-    // every candidate briefly, then the four fastest again with more runs
+    // pass 1, batch-wide: every candidate briefly, then the four fastest again with more runs
     std::vector<std::pair<float, int>> score;
     for (int i = 0; i < (int)cand.size() && rc == PCAL_OK; ++i) {
         const float ms = time_cand(cand[i], 2);
@@ -1268,6 +1300,38 @@ extern "C" int pcal_batch_autotune(pcal_batch* b, const void* const* samples, co
         if (ms >= 0.f && ms < best) {
             best = ms;
             best_s = cand[score[k].second];
+        }
+    }
+    // a change is kept when it is faster by more than the timing noise
+    auto try_cand = [&](const pcal_schedule& cs) {
+        const float ms = time_cand(cs, 6);
+        if (ms >= 0.f && ms < best * 0.995f) {
+            best = ms;
+            best_s = cs;
+        }
+    };
+    // pass 2: the CTA count of the one launch (SMs left idle can shorten the tail of a
+    // launch whose work does not divide evenly)
+    if (rc == PCAL_OK && best < 1e30f) {
+        for (int less : {8, 16}) {
+            if (b->num_sms - less < 1 || rc != PCAL_OK) continue;
+            pcal_schedule cs = best_s;
+            cs.ctas = b->num_sms - less;
+            try_cand(cs);
+        }
+    }
+    // pass 3: per (format, row width) bucket the batch occupies, the bucket's own width cap
+    bool occupied[PCAL_SCHED_BUCKETS] = {};
+    for (const BatchChan& C : ch_keep) occupied[sched_bucket(C.fmt, C.cols_total)] = true;
+    for (int bk = 0; bk < PCAL_SCHED_BUCKETS && rc == PCAL_OK && best < 1e30f; ++bk) {
+        if (!occupied[bk]) continue;
+        const pcal_schedule base = best_s;
+        for (int cap : {64, 128, 224}) {
+            const int now = base.col_cap_bucket[bk] > 0 ? base.col_cap_bucket[bk] : base.col_cap;
+            if (rc != PCAL_OK || cap == now) continue;  // the cap the bucket already has
+            pcal_schedule cs = base;
+            cs.col_cap_bucket[bk] = cap;
+            try_cand(cs);
         }
     }
     cudaEventDestroy(e0);

@@ -248,6 +248,6 @@ cudaError_t batch_launch_fold(const BatchCallDesc& d, void* d_desc, BatchChan* d
                               int* launches);
 cudaError_t batch_prepare_fold();
 cudaError_t batch_launch_tables(BatchChan& C, const pcal_geometry& g, cudaStream_t s);
-void batch_fill_chan(BatchChan& C, const pcal_geometry& g, double f_comb, int col_cap);
+void batch_fill_chan(BatchChan& C, const pcal_geometry& g, double f_comb, const pcal_schedule& sched);
 size_t batch_chan_bytes(const pcal_geometry& g);
 void batch_place_chan(BatchChan& C, const pcal_geometry& g, uint8_t* base);

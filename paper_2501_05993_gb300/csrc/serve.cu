@@ -258,7 +258,7 @@ void admit_queued(pcal_server* s) {
         st.slot = slot;
         s->slot_owner[slot] = st.id;
         BatchChan& C = s->h_ch[slot];
-        batch_fill_chan(C, st.g, st.desc.f_comb, s->sched.col_cap);
+        batch_fill_chan(C, st.g, st.desc.f_comb, s->sched);
         uint8_t* base = s->d_mem + off;
         batch_place_chan(C, st.g, base);
         const size_t chan_bytes = batch_chan_bytes(st.g);
@@ -404,7 +404,7 @@ extern "C" int pcal_server_create(const pcal_server_config* cfg, pcal_server** o
     pcal_server* s = new (std::nothrow) pcal_server();
     if (!s) return PCAL_ENOMEM;
     s->cfg = *cfg;
-    s->sched = pcal_schedule{0, 32, 0, 90, 4, 224};
+    s->sched = pcal_schedule{0, 32, 0, 90, 4, 224, {}};
     s->slot_owner.assign(cfg->max_streams, -1);
     cudaError_t e = cudaGetDevice(&s->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
@@ -426,6 +426,26 @@ extern "C" int pcal_server_create(const pcal_server_config* cfg, pcal_server** o
     for (int k = 0; k < kSlots && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&s->desc_ev[k], cudaEventDisableTiming);
     if (e == cudaSuccess) e = batch_prepare_fold();
     if (e == cudaSuccess) e = prepare_batch_finalize();
+    // First use must not stall a live stream: load the gather kernel now (modules load lazily, on first
+    // launch) and size the pinned piece list and the descriptor buffers for every stream at once.
+    if (e == cudaSuccess) {
+        cudaFuncAttributes fa;
+        e = cudaFuncGetAttributes(&fa, gather_kernel);
+    }
+    if (e == cudaSuccess) {
+        const int cap = 16 * cfg->max_streams;
+        e = cudaHostAlloc(reinterpret_cast<void**>(&s->h_pieces), sizeof(CopyPiece) * cap, cudaHostAllocMapped);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->d_pieces), s->h_pieces, 0);
+        if (e == cudaSuccess) s->pieces_cap = cap;
+    }
+    if (e == cudaSuccess) {
+        const size_t cap = align_up((size_t)cfg->max_streams * 8192 + 65536, 4096);
+        for (int k = 0; k < kSlots && e == cudaSuccess; ++k) {
+            e = cudaMallocHost(&s->h_desc[k], cap);
+            if (e == cudaSuccess) e = cudaMalloc(&s->d_desc[k], cap);
+        }
+        if (e == cudaSuccess) s->desc_cap = cap;
+    }
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         const bool oom = e == cudaErrorMemoryAllocation;

@@ -160,6 +160,7 @@ def test_batch_tensor_core_dft(pcal, mode):
     dict(ctas=152, box_rows=32, static_pct=0, min_chunk=1, col_cap=224),
     dict(ctas=37, box_rows=64, static_pct=100, min_chunk=8, col_cap=128),
     dict(ctas=300, box_rows=32, static_pct=60, min_chunk=3, col_cap=128, stages=3),
+    dict(ctas=136, box_rows=64, static_pct=90, min_chunk=16, col_cap=224, col_cap_bucket=[64, 128, 64, 0, 224, 64, 128, 64]),
 ])
 def test_batch_schedule_does_not_change_bins(pcal, sched):
     hosts = make_inputs(CHANNELS, seed=9)
@@ -246,6 +247,34 @@ def test_batch_graph_replay(pcal, mode):
                 check_results(b, c, ch, h, n0=period * ch[4])
 
 
+def expected_tiling(cols: int, cap: int):
+    """Column groups of a row of `cols` words under a width cap: as few groups as the cap allows, of equal width
+    rounded up to 8 words."""
+    gc = -(-cols // cap)
+    cw = min(cap, -(-(-(-cols // gc)) // 8) * 8)
+    return cw, -(-cols // cw)
+
+
+def test_batch_bucket_caps_cut_each_channel(pcal):
+    """Every channel's rows are cut by its own bucket's cap (format x row width), else by col_cap; a cap
+    outside {0, 64, 128, 224} is refused."""
+    with pcal.Batch([c[:4] for c in CHANNELS]) as b:
+        caps = [64, 128, 224, 64, 128, 64, 0, 224]
+        b.set_schedule(col_cap=128, col_cap_bucket=caps)
+        assert b.schedule["col_cap_bucket"] == caps
+        for c in range(len(CHANNELS)):
+            t = b.channel_tiling(c)
+            g = b.geometry[c]
+            cols = int(g.row_samples) // (16 if CHANNELS[c][3] == "2bit" else 4)
+            cls = 0 if cols <= 256 else 1 if cols <= 1024 else 2 if cols <= 4096 else 3
+            assert t["bucket"] == (4 if CHANNELS[c][3] == "i8" else 0) + cls
+            cap = caps[t["bucket"]] or 128
+            assert (t["col_width"], t["col_groups"]) == expected_tiling(cols, cap), (c, t, cols, cap)
+        with pytest.raises(pcal.PcalError):
+            b.set_schedule(col_cap_bucket=[0, 0, 0, 96, 0, 0, 0, 0])
+        assert b.schedule["col_cap_bucket"] == caps
+
+
 def test_batch_autotune_keeps_results(pcal):
     hosts = make_inputs(CHANNELS, seed=50)
     keep, ptrs = upload(CHANNELS, hosts)
@@ -253,7 +282,17 @@ def test_batch_autotune_keeps_results(pcal):
     with pcal.Batch([c[:4] for c in CHANNELS]) as b:
         chosen = b.autotune(ptrs, n)
         assert chosen["box_rows"] in (32, 64) and chosen["col_cap"] in (128, 224)
+        import torch
+
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        assert chosen["ctas"] == 0 or sms - chosen["ctas"] in (8, 16)
+        assert all(v in (0, 64, 128, 224) for v in chosen["col_cap_bucket"])
         assert b.schedule == chosen
+        for c in range(len(CHANNELS)):  # the chosen caps are the ones the channels are cut by
+            t = b.channel_tiling(c)
+            cols = int(b.geometry[c].row_samples) // (16 if CHANNELS[c][3] == "2bit" else 4)
+            cap = chosen["col_cap_bucket"][t["bucket"]] or chosen["col_cap"]
+            assert (t["col_width"], t["col_groups"]) == expected_tiling(cols, cap)
         for c in range(len(CHANNELS)):  # bins emptied again
             assert not np.any(b.bins(c)[:, 1:] if CHANNELS[c][3] == "2bit" else b.bins(c))
         b.accumulate(ptrs, n)

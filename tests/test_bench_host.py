@@ -29,6 +29,10 @@ def test_clock_record_flags_slowdowns():
 
 
 def test_traffic_only_while_the_source_matches(tmp_path, monkeypatch):
+    """A summary stamped with the kernel source's sha256 yields its DRAM bytes; any change to the source
+    withdraws them (the committed summary is checked against the committed source the same way)."""
+    import hashlib
+
     summary = open(os.path.join(bench.ROOT, "profiles", "fold2bit_c2_dram.txt")).read()
     recorded = int(summary.split("dram_bytes_per_launch=")[1].split()[0])
     root = tmp_path / "repo"
@@ -36,6 +40,9 @@ def test_traffic_only_while_the_source_matches(tmp_path, monkeypatch):
     csrc = root / "paper_2501_05993_gb300" / "csrc"
     csrc.mkdir(parents=True)
     shutil.copy(os.path.join(bench.ROOT, "paper_2501_05993_gb300", "csrc", "fold_bulk.cu"), csrc / "fold_bulk.cu")
+    sha = hashlib.sha256((csrc / "fold_bulk.cu").read_bytes()).hexdigest()
+    lines = [f"source_sha256={sha}" if l.startswith("source_sha256=") else l for l in summary.splitlines()]
+    (root / "profiles" / "fold2bit_c2_dram.txt").write_text("\n".join(lines) + "\n")
     monkeypatch.setattr(bench, "ROOT", str(root))
     assert bench.read_traffic("fold_bulk.cu") == recorded  # same source: the recorded figure
     with open(csrc / "fold_bulk.cu", "a") as f:
