@@ -386,7 +386,8 @@ extern "C" const double* pcal_result_device(const pcal_plan* p) { return p ? p->
 extern "C" int pcal_get_bins(pcal_plan* p, void* host_out) {
     if (!p || !host_out) return PCAL_EINVAL;
     const int64_t L = p->g.L;
-    cudaError_t e = cudaStreamSynchronize(p->last_stream);
+    cudaError_t e = flush_partials(p, p->last_stream);  // float32: pending fold partials into the bins
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->last_stream);
     if (e != cudaSuccess) return cuda_status(e);
     if (p->g.format == PCAL_I8) return cuda_status(cudaMemcpy(host_out, cur_acc8(p), L * 8, cudaMemcpyDeviceToHost));
     if (p->g.format == PCAL_F32) {

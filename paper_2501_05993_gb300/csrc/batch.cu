@@ -146,7 +146,9 @@ __global__ void __launch_bounds__(kMaxBlock, 1) batch_fold_kernel(const BatchFol
     const int q = tid / group_threads;
     const int col = tid % group_threads;
 
-    // producer state, kept across runs
+    // producer state, kept across runs; the samples are read once, so their
+    // L2 lines go first (the bins and tables the finalize reuses stay)
+    const uint64_t policy = producer ? l2_policy_evict_first() : 0ull;
     long long st_pos = (long long)blockIdx.x * a.static_boxes;
     long long st_end = st_pos + a.static_boxes;
     if (st_end > a.pool_start) st_end = a.pool_start;
@@ -211,8 +213,8 @@ __global__ void __launch_bounds__(kMaxBlock, 1) batch_fold_kernel(const BatchFol
                 const int st = pj % a.stages;
                 s_hdr[st] = 0;
                 mbar_arrive_expect_tx(&full[st], (uint32_t)seg.tx_bytes);
-                tma_load_2d(smem + (size_t)st * a.stage_stride, &a.maps[seg.map], seg.col0,
-                            (int)(pending - seg.box_start) * a.box_rows, &full[st]);
+                tma_load_2d_hint(smem + (size_t)st * a.stage_stride, &a.maps[seg.map], seg.col0,
+                                 (int)(pending - seg.box_start) * a.box_rows, &full[st], policy);
                 s_last_fill[st] = pj;
                 s_fill_open[st] = 1;
                 ++pj;

@@ -58,6 +58,12 @@ struct FinArgs {
     unsigned long long* wide2;
     long long* acc8;
     float2* accf;  // float32 bins in df (hi, lo)
+    // float32: fold partials not yet added into accf (slot e: [pf_rg[e]][pf_cols], column 0 = bin pf_ka[e])
+    const float2* pf[kPartSlots];
+    int64_t pf_rg[kPartSlots];
+    int64_t pf_ka[kPartSlots];
+    int n_pf;
+    int64_t pf_cols;
     const long long* counts4;  // no-allocation entry: the caller's counts [L][4]
     double lev[4];             // no-allocation entry: the code levels
     const double2* tw;
@@ -96,7 +102,21 @@ __device__ __forceinline__ double read_bin(const FinArgs& a, int64_t k) {
     }
     if (a.fmt == PCAL_I8) return (double)a.acc8[k];
     const float2 v = a.accf[k];
-    return (double)v.x + (double)v.y;
+    if (a.n_pf == 0) return (double)v.x + (double)v.y;
+    // the pending fold partials of this bin, slot by slot, row group by row
+    // group, in double-float (a fixed order: the result does not depend on
+    // timing)
+    df s{v.x, v.y};
+    for (int e = 0; e < a.n_pf; ++e) {
+        for (int64_t c = ((k - a.pf_ka[e]) % a.L + a.L) % a.L; c < a.pf_cols; c += a.L) {
+            const float2* col = a.pf[e] + c;
+            for (int64_t rg = 0; rg < a.pf_rg[e]; ++rg) {
+                const float2 w = col[rg * a.pf_cols];
+                s = pcal_df::add(s, pcal_df::two_sum(w.x, w.y));
+            }
+        }
+    }
+    return (double)s.hi + (double)s.lo;
 }
 
 // exp(-j*2*pi*m/L): the plan's table; NoAlloc evaluates it here.
@@ -1273,6 +1293,15 @@ cudaError_t launch_finalize(pcal_plan* p, cudaStream_t s) {
     a.wide2 = cur_wide2(p);
     a.acc8 = cur_acc8(p);
     a.accf = cur_accf(p);
+    if (g.format == PCAL_F32) {
+        for (int e = 0; e < p->n_pending; ++e) {
+            a.pf[e] = p->pending[e].base;
+            a.pf_rg[e] = p->pending[e].row_groups;
+            a.pf_ka[e] = p->pending[e].k_a;
+        }
+        a.n_pf = p->n_pending;
+        a.pf_cols = g.row_samples / g.samples_per_byte_x4;
+    }
     a.tw = p->d_tw;
     a.twN = p->d_twN;
     a.P = reinterpret_cast<float4*>(p->d_P);
@@ -1280,16 +1309,22 @@ cudaError_t launch_finalize(pcal_plan* p, cudaStream_t s) {
     a.res = p->d_res;
     a.extra = p->d_res + 5 * g.N + 3;
     a.ticket = p->d_ticket;
+    cudaError_t e = cudaErrorUnknown;
+    bool done = false;
     if (g.N <= kClusterMaxN && g.L <= kClusterMaxL) {
         const int C = cluster_size_for_device();
         if (C > 0) {
             p->stats.kernel_launches += 1;
-            return launch_cluster_finalize(a, C, s);
+            e = launch_cluster_finalize(a, C, s);
+            done = true;
         }
     }
-    int launches = 0;
-    cudaError_t e = launch_finalize_args<false>(a, p->num_sms, s, &launches);
-    p->stats.kernel_launches += launches;
+    if (!done) {
+        int launches = 0;
+        e = launch_finalize_args<false>(a, p->num_sms, s, &launches);
+        p->stats.kernel_launches += launches;
+    }
+    if (e == cudaSuccess) p->n_pending = 0;  // the finalize added them (and clears the bins)
     return e;
 }
 

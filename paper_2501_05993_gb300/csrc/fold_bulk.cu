@@ -218,6 +218,9 @@ __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_co
         // then chunks from the column group's counter until the work or the
         // per-CTA cap runs out.  Local box j goes to stage j % stages.
         if (tid % 32 == 0) {
+            // the samples are read once: their L2 lines go first, so the
+            // stream does not evict the bins and tables the finalize reuses
+            const uint64_t policy = l2_policy_evict_first();
             // the next launch's read start (used at the end; loaded now so
             // that the latency of host memory hides behind the first copies)
             unsigned long long hint0 = 0, hint1 = 0, hint2 = 0;
@@ -243,7 +246,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_co
                 if (!stage_free(j)) return false;
                 const int s = j % a.stages;
                 mbar_arrive_expect_tx(&full[s], a.tx_bytes);
-                tma_load_2d(smem + (size_t)s * a.stage_stride, &tmap, c0, box * a.box_rows, &full[s]);
+                tma_load_2d_hint(smem + (size_t)s * a.stage_stride, &tmap, c0, box * a.box_rows, &full[s], policy);
                 s_last_fill[s] = j;
                 s_fill_open[s] = 1;
                 ++j;
@@ -505,44 +508,55 @@ __global__ void __launch_bounds__(kMaxBlock, 1) bulk_fold_kernel(const __grid_co
     grid_dependency_wait();
 }
 
-// f32: bin k = sum over row groups and over the columns that map to k, in a
-// fixed order and in double-float, added to the plan's double-float bins.
-// One warp per bin: lane j sums terms j, j + 32, ... (row group major), then
-// a fixed shuffle tree adds the lanes, so the partials are loaded 32 at a time
-// instead of one after another (a thread per bin waited out 19 dependent L2
-// loads per launch on a 64 MB input) and the result does not depend on
-// timing.  Launched as a programmatic dependent of the fold: it lets the next
-// kernel start launching, then waits for the fold's partials.
-constexpr int kReduceWarps = 8;  // bins per block
+// f32: bin k += the sum over the pending slots, their row groups and the
+// columns that map to k, in a fixed order and in double-float.  One warp per
+// bin: lane j sums terms j, j + 32, ... (slot, then row group major), then a
+// fixed shuffle tree adds the lanes, so the partials are loaded 32 at a time
+// (a thread per bin waited out 19 dependent L2 loads per slot on a 64 MB
+// input) and the result does not depend on timing.  Launched as a
+// programmatic dependent of the preceding kernel: it lets the next kernel
+// start launching, then waits for the partials.  The next kernel can launch
+// only once every block of this one has started, so the grid is at most one
+// block per SM and its warps stride over the bins.
+constexpr int kReduceWarps = 16;  // warps per block
 
-__global__ void __launch_bounds__(32 * kReduceWarps) reduce_f32_kernel(const float2* __restrict__ part,
-                                                                      int64_t row_groups, int cols_total,
-                                                                      int64_t k_a, int64_t L,
-                                                                      float2* __restrict__ acc) {
+struct PendingArgs {
+    const float2* base[kPartSlots];
+    int64_t row_groups[kPartSlots];
+    int64_t k_a[kPartSlots];
+    int n;
+};
+
+__global__ void __launch_bounds__(32 * kReduceWarps) reduce_f32_kernel(const PendingArgs pa, int cols_total,
+                                                                      int64_t L, float2* __restrict__ acc) {
     allow_dependents();
     grid_dependency_wait();
-    const int64_t k = blockIdx.x * (int64_t)kReduceWarps + threadIdx.x / 32;
     const int lane = threadIdx.x & 31;
-    if (k >= L) return;  // whole warps leave together
-    const int64_t c_first = ((k - k_a) % L + L) % L;
-    if (c_first >= cols_total) return;
-    const int64_t per_rg = (cols_total - 1 - c_first) / L + 1;  // columns of this bin in a row
-    const int64_t terms = row_groups * per_rg;
-    pcal_df::df s{0.f, 0.f};
-    for (int64_t t = lane; t < terms; t += 32) {
-        const int64_t rg = t / per_rg, c = c_first + (t % per_rg) * L;
-        const float2 v = part[rg * cols_total + c];
-        s = pcal_df::add(s, pcal_df::two_sum(v.x, v.y));
-    }
+    const int64_t warps = (int64_t)gridDim.x * kReduceWarps;
+    for (int64_t k = blockIdx.x * (int64_t)kReduceWarps + threadIdx.x / 32; k < L; k += warps) {
+        pcal_df::df s{0.f, 0.f};
+        for (int e = 0; e < pa.n; ++e) {
+            const int64_t c_first = ((k - pa.k_a[e]) % L + L) % L;
+            if (c_first >= cols_total) continue;  // whole warps skip together
+            const int64_t per_rg = (cols_total - 1 - c_first) / L + 1;  // columns of this bin in a row
+            const int64_t terms = pa.row_groups[e] * per_rg;
+            for (int64_t t = lane; t < terms; t += 32) {
+                const int64_t rg = t / per_rg, c = c_first + (t % per_rg) * L;
+                const float2 v = pa.base[e][rg * cols_total + c];
+                s = pcal_df::add(s, pcal_df::two_sum(v.x, v.y));
+            }
+        }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const pcal_df::df o{__shfl_down_sync(0xffffffffu, s.hi, off), __shfl_down_sync(0xffffffffu, s.lo, off)};
-        s = pcal_df::add(s, o);
-    }
-    if (lane == 0) {
-        const float2 a = acc[k];
-        s = pcal_df::add(pcal_df::df{a.x, a.y}, s);
-        acc[k] = make_float2(s.hi, s.lo);
+        for (int off = 16; off > 0; off >>= 1) {
+            const pcal_df::df o{__shfl_down_sync(0xffffffffu, s.hi, off),
+                                __shfl_down_sync(0xffffffffu, s.lo, off)};
+            s = pcal_df::add(s, o);
+        }
+        if (lane == 0) {
+            const float2 a = acc[k];
+            s = pcal_df::add(pcal_df::df{a.x, a.y}, s);
+            acc[k] = make_float2(s.hi, s.lo);
+        }
     }
 }
 
@@ -715,6 +729,35 @@ void unpublish_hint(pcal_plan* p, unsigned int epoch) {
 
 }  // namespace
 
+cudaError_t flush_partials(pcal_plan* p, cudaStream_t s) {
+    if (p->g.format != PCAL_F32 || p->n_pending == 0) return cudaSuccess;
+    PendingArgs pa{};
+    for (int e = 0; e < p->n_pending; ++e) {
+        pa.base[e] = p->pending[e].base;
+        pa.row_groups[e] = p->pending[e].row_groups;
+        pa.k_a[e] = p->pending[e].k_a;
+    }
+    pa.n = p->n_pending;
+    const int spw = p->g.samples_per_byte_x4;
+    const int cols_total = (int)(p->g.row_samples / spw);
+    const int64_t blocks = (p->g.L + kReduceWarps - 1) / kReduceWarps;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(blocks < p->num_sms ? blocks : p->num_sms));
+    cfg.blockDim = dim3(32 * kReduceWarps);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, reduce_f32_kernel, pa, cols_total, (int64_t)p->g.L, cur_accf(p));
+    if (e == cudaSuccess) {
+        p->n_pending = 0;
+        p->stats.kernel_launches += 1;
+    }
+    return e;
+}
+
 cudaError_t launch_bulk(pcal_plan* p, const void* d_rows, int64_t n_rows, int64_t k_a, cudaStream_t s, int* launched) {
     *launched = 0;
     const BulkMapEntry* hit = nullptr;
@@ -792,38 +835,35 @@ cudaError_t launch_bulk(pcal_plan* p, const void* d_rows, int64_t n_rows, int64_
     const int grid = (int)(t.col_groups * t.row_groups);
     cudaError_t e;
     if (p->g.format == PCAL_F32) {
+        // the partials go to the next free slot; they are added into the bins
+        // by the finalize (or by a reduce launch when the slots run out)
         const size_t need = (size_t)t.row_groups * t.cols_total;
-        if (need > p->partf_cap) {
-            cudaFree(p->d_partf);
+        e = cudaSuccess;
+        if (p->n_pending == kPartSlots || (need > p->partf_cap && p->n_pending > 0)) e = flush_partials(p, s);
+        if (e == cudaSuccess && need > p->partf_cap) {
+            cudaFree(p->d_partf);  // (waits for the device: no kernel reads the old slots afterwards)
             p->d_partf = nullptr;
             p->partf_cap = 0;
-            e = cudaMalloc(&p->d_partf, need * sizeof(float2));
-            if (e != cudaSuccess) {
-                unpublish_hint(p, a.epoch);
-                return e;
-            }
-            p->partf_cap = need;
+            e = cudaMalloc(&p->d_partf, kPartSlots * need * sizeof(float2));
+            if (e == cudaSuccess) p->partf_cap = need;
+            p->part_next = 0;
         }
-        a.partf = p->d_partf;
+        if (e != cudaSuccess) {
+            unpublish_hint(p, a.epoch);
+            return e;
+        }
+        const int slot = p->part_next;
+        a.partf = p->d_partf + (size_t)slot * p->partf_cap;
         e = launch_one<PCAL_F32, 1>(map, a, grid, t.threads, t.smem_bytes, s);
         if (e != cudaSuccess) {
             unpublish_hint(p, a.epoch);
             return e;
         }
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)((p->g.L + kReduceWarps - 1) / kReduceWarps));
-        cfg.blockDim = dim3(32 * kReduceWarps);
-        cfg.stream = s;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-        attr[0].val.programmaticStreamSerializationAllowed = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, reduce_f32_kernel, (const float2*)p->d_partf, (int64_t)t.row_groups,
-                               (int)t.cols_total, (int64_t)k_a, (int64_t)p->g.L, cur_accf(p));
-        *launched = 2;
-        p->stats.kernel_launches += 2;
-        return e;
+        p->part_next = (slot + 1) % kPartSlots;
+        p->pending[p->n_pending++] = PartSlot{a.partf, (int64_t)t.row_groups, k_a};
+        *launched = 1;
+        p->stats.kernel_launches += 1;
+        return cudaSuccess;
     }
     if (p->g.format == PCAL_I8) {
         e = launch_one<PCAL_I8, 1>(map, a, grid, t.threads, t.smem_bytes, s);

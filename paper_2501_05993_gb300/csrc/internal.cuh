@@ -72,6 +72,18 @@ struct PrefetchHint {
 };
 __host__ __device__ inline unsigned long long hint_tag(unsigned long long epoch) { return epoch % 65535ull + 1ull; }
 
+// Float32 bulk folds write per-tile partial sums into one of kPartSlots
+// slots; the finalize adds the pending slots to the bins as it reads them,
+// and a reduce kernel adds them when the slots run out or the host reads the
+// bins, so consecutive folds (and a fold and its finalize) follow each other
+// with no kernel in between.
+constexpr int kPartSlots = 4;
+struct PartSlot {
+    const float2* base;  // [row_groups][cols_total]
+    int64_t row_groups;
+    int64_t k_a;         // bin of column 0
+};
+
 struct pcal_plan {
     pcal_geometry g;
     double levels[4];
@@ -91,8 +103,11 @@ struct pcal_plan {
     unsigned long long* d_wide2;  // 2-bit spilled counts [2][3][L]
     long long* d_acc8;            // int8 sums [2][L]
     float2* d_accf;               // float32 sums as double-float (hi, lo) [2][L]
-    float2* d_partf;              // float32 per-tile partial sums (scratch)
-    size_t partf_cap;             // capacity of d_partf in float2
+    float2* d_partf;              // float32 per-tile partial sums: kPartSlots slots of partf_cap float2
+    size_t partf_cap;             // capacity of one slot in float2
+    PartSlot pending[kPartSlots]; // slots written by folds and not yet added into the bins
+    int n_pending;
+    int part_next;                // slot of the next float32 fold
     double2* d_tw;                // exp(-j 2 pi m / L), m < L
     float2* d_twN;                // exp(-j 2 pi m / N), m < N (FP32)
     double2* d_P;                 // folded rotated bins P[b], b < N (scratch)
@@ -133,6 +148,8 @@ cudaError_t launch_ragged(pcal_plan* p, const uint8_t* d_bytes, int64_t n_sample
 cudaError_t launch_spill2(pcal_plan* p, cudaStream_t s);
 cudaError_t launch_export_bins(pcal_plan* p, void* d_out, cudaStream_t s);
 cudaError_t launch_finalize(pcal_plan* p, cudaStream_t s);
+// Add a float32 plan's pending partial slots into its bins (one reduce launch; none when nothing is pending).
+cudaError_t flush_partials(pcal_plan* p, cudaStream_t s);
 
 // Bulk fold of whole rows of row_samples samples starting at a 16-byte
 // aligned device address whose first sample has phase k_a = n mod L.

@@ -267,6 +267,33 @@ def test_pipelined_host_periods(pcal):
         assert abs(r["td"] - pr["td"]) <= 1e-3 * pr["sigma_td"]
 
 
+def test_f32_partial_slots_across_many_calls(pcal):
+    """Float32 folds leave per-tile partials in a ring of slots that the
+    finalize adds into the bins: seven calls of growing size in one period
+    (the ring fills and is flushed, the slots are reallocated larger), a host
+    read of the bins in the middle (which adds the pending slots first), then
+    the finalize, against the oracle; a second period starts from empty bins."""
+    fs, fc, fo = PLANS["c1"]
+    sizes = [300_001, 1_200_000, 900_003, 2_500_000, 700_000, 1_800_017, 3_100_000]
+    host = synth.Stream(fs=fs, fc=fc, fo=fo, amp=0.05, td=3.7e-9, seed=41).f32(0, sum(sizes) + 1_000_000)
+    with pcal.Plan(fs, fc, fo, "f32") as p:
+        keep, addr = to_dev(host)
+        n0 = 0
+        for i, n in enumerate(sizes):
+            p.accumulate(addr + 4 * n0, n)
+            n0 += n
+            if i == 3:  # mid-period host read
+                check_bins(p.bins(), oracle.sums_f32(host[:n0], 0, p.L), "f32", host[:n0], p.L)
+        check_bins(p.bins(), oracle.sums_f32(host[:n0], 0, p.L), "f32", host[:n0], p.L)
+        p.accumulate(addr + 4 * n0, 900_000)  # pending again when the period ends
+        T = p.finalize()
+        m = n0 + 900_000
+        check_phasors(T, oracle.tones_from_bins(oracle.sums_f32(host[:m], 0, p.L), fs, fc, fo))
+        p.accumulate(addr + 4 * m, 100_000)
+        T2 = p.finalize()
+    check_phasors(T2, oracle.direct(host[m:m + 100_000], "f32", m, fs, fc, fo))
+
+
 def test_f32_is_deterministic(pcal):
     fs, fc, fo = PLANS["c1"]
     n = 4_000_000 + 17
