@@ -108,10 +108,20 @@ __device__ __forceinline__ double read_bin(const FinArgs& a, int64_t k) {
     // timing)
     df s{v.x, v.y};
     for (int e = 0; e < a.n_pf; ++e) {
+        const int64_t R = a.pf_rg[e], stride = a.pf_cols;
         for (int64_t c = ((k - a.pf_ka[e]) % a.L + a.L) % a.L; c < a.pf_cols; c += a.L) {
             const float2* col = a.pf[e] + c;
-            for (int64_t rg = 0; rg < a.pf_rg[e]; ++rg) {
-                const float2 w = col[rg * a.pf_cols];
+            int64_t rg = 0;
+            // eight loads in flight, then their additions in row-group order
+            for (; rg + 8 <= R; rg += 8) {
+                float2 w[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) w[u] = col[(rg + u) * stride];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) s = pcal_df::add(s, pcal_df::two_sum(w[u].x, w[u].y));
+            }
+            for (; rg < R; ++rg) {
+                const float2 w = col[rg * stride];
                 s = pcal_df::add(s, pcal_df::two_sum(w.x, w.y));
             }
         }

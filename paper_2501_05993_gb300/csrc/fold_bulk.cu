@@ -635,19 +635,38 @@ int bulk_tiling(const pcal_plan* p, int64_t n_rows, BulkTiling* t) {
         }
         if (w <= 32) break;
     }
+    // An even cut where one exists: equal column groups stream equal bytes
+    // (work is balanced within a column group, not across them; C1 float32:
+    // 7 groups of 232 words left the 208-word group's CTAs idle at the end,
+    // 8 of 200 fill 136 CTAs), if it fills the SMs at least as well.
+    {
+        auto fill = [&](int g) { return g * (sms_fold / g > 0 ? sms_fold / g : 1); };
+        for (int g = gc; g <= 2 * gc && g <= cols; ++g) {
+            if (cols % g != 0 || (cols / g) % 8 != 0 || cols / g > 256) continue;
+            if (g == gc && cols / g == cw) break;  // already even
+            if (fill(g) >= fill(gc)) {
+                gc = g;
+                cw = cols / g;
+            }
+            break;
+        }
+    }
     z.col_width = cw;
     z.col_groups = gc;
     const int wpr = (cw + 31) / 32;
     int r_max = (kMaxBlock / 32 - 1) / wpr;
     if (r_max > 8) r_max = 8;
     if (r_max < 1) r_max = 1;
-    // 2-bit: a stage of about 48-64 KB of whole 32-row blocks (each TMA box
-    // copy costs the producer a fixed ~0.3 us to issue, whatever its size, so
-    // fewer, larger boxes fill the pipeline sooner after a launch: short
-    // launches are 2-bit); int8 / f32: about 24-32 KB, which keeps 2 replica
-    // groups and 8 stages on wide rows
+    // 2-bit and float32: a stage of about 48-64 KB (2-bit: whole 32-row
+    // blocks).  Each TMA box copy costs the producer a fixed ~0.3 us to issue
+    // under load, whatever its size, so fewer, larger boxes keep up with the
+    // consumers and fill the pipeline sooner after a launch (float32 C1:
+    // 22 KB boxes held a CTA to ~48 GB/s, 51 KB boxes took the fold from
+    // 12.95 to 12.28 us).  int8: about 24-32 KB, which keeps 2 replica groups
+    // and 8 stages on wide rows (its 1 GiB folds run at 0.98 of the copy
+    // bandwidth).
     const int unit = p->g.format == PCAL_2BIT ? 32 : 8;
-    int units = (p->g.format == PCAL_2BIT ? 56 * 1024 : 28 * 1024) / (unit * cw * 4);
+    int units = (p->g.format != PCAL_I8 ? 56 * 1024 : 28 * 1024) / (unit * cw * 4);
     if (units < 1) units = 1;
     int box = unit * units;
     while (box > 256) box -= unit;
