@@ -77,6 +77,34 @@ struct FinArgs {
     unsigned int* ticket;
 };
 
+// A float32 bin plus its pending fold partials, slot by slot, row group by
+// row group, in double-float (a fixed order: the result does not depend on
+// timing).  Out of line: the finalize's bin loops are latency-bound and their
+// code stays small for the other formats.
+__device__ __noinline__ double f32_with_pending(const FinArgs& a, int64_t k, float2 v) {
+    df s{v.x, v.y};
+    for (int e = 0; e < a.n_pf; ++e) {
+        const int64_t R = a.pf_rg[e], stride = a.pf_cols;
+        for (int64_t c = ((k - a.pf_ka[e]) % a.L + a.L) % a.L; c < a.pf_cols; c += a.L) {
+            const float2* col = a.pf[e] + c;
+            int64_t rg = 0;
+            // eight loads in flight, then their additions in row-group order
+            for (; rg + 8 <= R; rg += 8) {
+                float2 w[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) w[u] = col[(rg + u) * stride];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) s = pcal_df::add(s, pcal_df::two_sum(w[u].x, w[u].y));
+            }
+            for (; rg < R; ++rg) {
+                const float2 w = col[rg * stride];
+                s = pcal_df::add(s, pcal_df::two_sum(w.x, w.y));
+            }
+        }
+    }
+    return (double)s.hi + (double)s.lo;
+}
+
 // Decode bin k to its real value S[k] (FP64).  NoAlloc: the caller's
 // per-(bin, code) counts.
 template <bool NoAlloc>
@@ -103,30 +131,7 @@ __device__ __forceinline__ double read_bin(const FinArgs& a, int64_t k) {
     if (a.fmt == PCAL_I8) return (double)a.acc8[k];
     const float2 v = a.accf[k];
     if (a.n_pf == 0) return (double)v.x + (double)v.y;
-    // the pending fold partials of this bin, slot by slot, row group by row
-    // group, in double-float (a fixed order: the result does not depend on
-    // timing)
-    df s{v.x, v.y};
-    for (int e = 0; e < a.n_pf; ++e) {
-        const int64_t R = a.pf_rg[e], stride = a.pf_cols;
-        for (int64_t c = ((k - a.pf_ka[e]) % a.L + a.L) % a.L; c < a.pf_cols; c += a.L) {
-            const float2* col = a.pf[e] + c;
-            int64_t rg = 0;
-            // eight loads in flight, then their additions in row-group order
-            for (; rg + 8 <= R; rg += 8) {
-                float2 w[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) w[u] = col[(rg + u) * stride];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) s = pcal_df::add(s, pcal_df::two_sum(w[u].x, w[u].y));
-            }
-            for (; rg < R; ++rg) {
-                const float2 w = col[rg * stride];
-                s = pcal_df::add(s, pcal_df::two_sum(w.x, w.y));
-            }
-        }
-    }
-    return (double)s.hi + (double)s.lo;
+    return f32_with_pending(a, k, v);
 }
 
 // exp(-j*2*pi*m/L): the plan's table; NoAlloc evaluates it here.

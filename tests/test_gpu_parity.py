@@ -151,6 +151,30 @@ def test_chunk_splits_are_invisible(pcal, fmt):
     assert np.array_equal(bins, oracle_bins(host, fmt, 0, p.L))
 
 
+@pytest.mark.parametrize("fmt", ["2bit", "i8", "f32"])
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_random_chunk_splits_and_offsets(pcal, fmt, seed):
+    """Random cut points (whole bytes for 2-bit) and random byte offsets of
+    each chunk's device buffer: the bins are those of the whole stream (exact
+    for 2-bit and int8), whatever mix of ragged and bulk work each call gets."""
+    rng = np.random.default_rng(100 + seed)
+    fs, fc, fo = PLANS["odd"] if seed == 2 else PLANS["c2"]
+    n = {"2bit": 4 * 1_500_000, "i8": 4_200_000, "f32": 2_000_000}[fmt]
+    q = 4 if fmt == "2bit" else 1
+    host = synth.Stream(fs=fs, fc=fc, fo=fo, amp=0.03, td=2e-9, seed=seed).samples(fmt, 0, n)
+    cuts = sorted(set([0, n] + [int(c) // q * q for c in rng.integers(1, n, 6)]))
+    with pcal.Plan(fs, fc, fo, fmt) as p:
+        keep = []
+        for a, b in zip(cuts[:-1], cuts[1:]):
+            part = host[a // q: b // q]
+            off = int(rng.integers(0, 16)) // (4 if fmt == "f32" else 1) * (4 if fmt == "f32" else 1)
+            kk, addr = to_dev(part, offset=off)
+            keep.append(kk)
+            p.accumulate(addr, b - a)
+        bins = p.bins()
+    check_bins(bins, oracle_bins(host, fmt, 0, p.L), fmt, host, p.L)
+
+
 def test_two_bit_levels_and_spill(pcal):
     """Small L forces the packed 21-bit fields to spill; custom levels."""
     fs, fc, fo = 16, 4, 1
