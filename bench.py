@@ -114,12 +114,12 @@ def read_batch_traffic_ratio():
         return None
 
 
-def read_traffic(kernel_file: str):
-    """Per-launch DRAM bytes of the fold kernel from the committed ncu
+def read_traffic(kernel_file: str, summary: str = "fold2bit_c2_dram.txt"):
+    """Per-launch DRAM bytes of a fold kernel from its committed ncu
     summary, or None when the kernel source changed since the capture."""
     import hashlib
 
-    path = os.path.join(ROOT, "profiles", "fold2bit_c2_dram.txt")
+    path = os.path.join(ROOT, "profiles", summary)
     try:
         lines = open(path).read().splitlines()
     except OSError:
@@ -835,8 +835,10 @@ def run_c1(args, emit=True, n_buffers=8):
            "config": {"workload": C1_WORKLOAD, "fold_ms": fold_ms, "td_s": res["td"], "sigma_td_s": res["sigma_td"],
                       "l2": f"inputs rotate over {n_buffers} device buffers ({n_buffers * nbytes >> 20} MB) > L2"},
            "roofline": {"bound": "hbm", "achieved": nbytes / (fold_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
-                        "frac": nbytes / (fold_ms / 1e3) / 1e9 / peak, "traffic": None,
-                        "peak_kind": f"{peak_kind} (copy bandwidth)", "kernel": "bulk_fold_kernel<f32> + reduce"}}
+                        "frac": nbytes / (fold_ms / 1e3) / 1e9 / peak,
+                        "traffic": read_traffic("fold_bulk.cu", "fold_f32_c1_dram.txt"),
+                        "peak_kind": f"{peak_kind} (copy bandwidth)", "kernel": "bulk_fold_kernel<f32> (+ the partial reduction, one per four folds)",
+                        "algorithmic_bytes_per_launch": nbytes}}
     if emit:
         print(json.dumps(out))
     return out

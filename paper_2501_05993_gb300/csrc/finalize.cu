@@ -77,34 +77,6 @@ struct FinArgs {
     unsigned int* ticket;
 };
 
-// A float32 bin plus its pending fold partials, slot by slot, row group by
-// row group, in double-float (a fixed order: the result does not depend on
-// timing).  Out of line: the finalize's bin loops are latency-bound and their
-// code stays small for the other formats.
-__device__ __noinline__ double f32_with_pending(const FinArgs& a, int64_t k, float2 v) {
-    df s{v.x, v.y};
-    for (int e = 0; e < a.n_pf; ++e) {
-        const int64_t R = a.pf_rg[e], stride = a.pf_cols;
-        for (int64_t c = ((k - a.pf_ka[e]) % a.L + a.L) % a.L; c < a.pf_cols; c += a.L) {
-            const float2* col = a.pf[e] + c;
-            int64_t rg = 0;
-            // eight loads in flight, then their additions in row-group order
-            for (; rg + 8 <= R; rg += 8) {
-                float2 w[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) w[u] = col[(rg + u) * stride];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) s = pcal_df::add(s, pcal_df::two_sum(w[u].x, w[u].y));
-            }
-            for (; rg < R; ++rg) {
-                const float2 w = col[rg * stride];
-                s = pcal_df::add(s, pcal_df::two_sum(w.x, w.y));
-            }
-        }
-    }
-    return (double)s.hi + (double)s.lo;
-}
-
 // Decode bin k to its real value S[k] (FP64).  NoAlloc: the caller's
 // per-(bin, code) counts.
 template <bool NoAlloc>
@@ -131,7 +103,31 @@ __device__ __forceinline__ double read_bin(const FinArgs& a, int64_t k) {
     if (a.fmt == PCAL_I8) return (double)a.acc8[k];
     const float2 v = a.accf[k];
     if (a.n_pf == 0) return (double)v.x + (double)v.y;
-    return f32_with_pending(a, k, v);
+    // the pending fold partials of this bin, slot by slot, row group by row
+    // group, in double-float (a fixed order: the result does not depend on
+    // timing).  Inline: out of line (a call per bin) the C1 step took
+    // 1.5 us longer.
+    df s{v.x, v.y};
+    for (int e = 0; e < a.n_pf; ++e) {
+        const int64_t R = a.pf_rg[e], stride = a.pf_cols;
+        for (int64_t c = ((k - a.pf_ka[e]) % a.L + a.L) % a.L; c < a.pf_cols; c += a.L) {
+            const float2* col = a.pf[e] + c;
+            int64_t rg = 0;
+            // eight loads in flight, then their additions in row-group order
+            for (; rg + 8 <= R; rg += 8) {
+                float2 w[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) w[u] = col[(rg + u) * stride];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) s = pcal_df::add(s, pcal_df::two_sum(w[u].x, w[u].y));
+            }
+            for (; rg < R; ++rg) {
+                const float2 w = col[rg * stride];
+                s = pcal_df::add(s, pcal_df::two_sum(w.x, w.y));
+            }
+        }
+    }
+    return (double)s.hi + (double)s.lo;
 }
 
 // exp(-j*2*pi*m/L): the plan's table; NoAlloc evaluates it here.
@@ -954,9 +950,12 @@ __device__ inline FinArgs batch_fin_args(const BatchChan& bc) {
 // Batch finalize: cluster c finalizes channel c of the batch from the
 // channel's device state, then starts the channel's next period.  split:
 // stop after P (stored in the channel's P slot) for the batched DFT; the
-// products kernel finishes the channel.
+// products kernel finishes the channel.  A programmatic dependent of the
+// fold: it waits for the fold's bins and indices before reading any state.
 __global__ void __launch_bounds__(kClusterThreads) batch_fin_kernel(BatchChan* ch, const int* list, int split) {
     namespace cg = cooperative_groups;
+    allow_dependents();
+    grid_dependency_wait();
     const int i = (int)(blockIdx.x / cg::this_cluster().num_blocks());
     const int c = list ? list[i] : i;
     BatchChan& bc = ch[c];
@@ -1263,13 +1262,15 @@ cudaError_t launch_batch_finalize(BatchChan* d_ch, int n_ch, int max_n, const in
     cfg.blockDim = dim3(kClusterThreads);
     cfg.dynamicSmemBytes = cluster_smem_bytes(max_n);
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = C;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     return cudaLaunchKernelEx(&cfg, batch_fin_kernel, d_ch, d_list, split);
 }
 

@@ -414,6 +414,7 @@ extern "C" int pcal_server_create(const pcal_server_config* cfg, pcal_server** o
     if (e == cudaSuccess) e = cudaMallocHost(&s->h_ch, sizeof(BatchChan) * cfg->max_streams);
     if (e == cudaSuccess) memset(static_cast<void*>(s->h_ch), 0, sizeof(BatchChan) * cfg->max_streams);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_ctr, 256);
+    if (e == cudaSuccess) e = cudaMemset(s->d_ctr, 0, 256);  // each fold leaves its counters zero
     if (e == cudaSuccess) e = cudaMalloc(&s->d_err, 256);
     if (e == cudaSuccess) e = cudaMemset(s->d_err, 0, 256);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking);

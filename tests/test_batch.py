@@ -220,6 +220,34 @@ def test_batch_two_calls_and_two_periods(pcal):
             check_results(b, c, ch, h, n0=ch[4])
 
 
+def test_batch_repeated_call_on_the_same_buffers(pcal):
+    """A call that repeats the previous call's buffers and lengths reuses its device descriptors: the samples are
+    read again and continue each channel's index (bins = the oracle over the stream twice over)."""
+    chans = CHANNELS
+    hosts = make_inputs(chans, seed=51)
+    keep, ptrs = upload(chans, hosts)
+    n = [ch[4] for ch in chans]
+    with pcal.Batch([c[:4] for c in chans]) as b:
+        for _ in range(3):
+            b.accumulate(ptrs, n)
+        for c, (ch, h) in enumerate(zip(chans, hosts)):
+            L = int(b.geometry[c].L)
+            count = oracle.counts_2bit if ch[3] == "2bit" else oracle.sums_i8
+            ref = sum(count(h, k * ch[4], L) for k in range(3))
+            bins = b.bins(c)
+            assert np.array_equal(bins, ref), f"channel {c}: bins differ at {np.argwhere(bins != ref)[:4].tolist()}"
+        b.finalize_device()
+        for c, (ch, h) in enumerate(zip(chans, hosts)):
+            if ch[4] == 0:
+                continue
+            fs, fc, fo, fmt = ch[:4]
+            L = int(b.geometry[c].L)
+            S = sum(oracle.bins(h, fmt, k * ch[4], L) for k in range(3))
+            ref = oracle.tones_from_bins(S, fs, fc, fo)
+            T = b.results(c)["phasors"]
+            assert np.max(np.abs(T - ref)) <= PHASOR_RTOL * np.max(np.abs(ref)), c
+
+
 @pytest.mark.parametrize("mode", ["fp32", "tf32x3"])
 def test_batch_graph_replay(pcal, mode):
     """A captured step replayed on refilled buffers gives each period's

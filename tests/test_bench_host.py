@@ -4,6 +4,8 @@ while the kernel source still matches the one the ncu summary was taken on."""
 import os
 import shutil
 
+import pytest
+
 import bench
 
 ROW = "0, {sm}, 2070, 900.5, 0x{mask}, {hw}, {hwt}, {swt}, {pcap}"
@@ -28,12 +30,13 @@ def test_clock_record_flags_slowdowns():
     assert bench.ClockSampler.parse("")["sm_mhz"] is None
 
 
-def test_traffic_only_while_the_source_matches(tmp_path, monkeypatch):
+@pytest.mark.parametrize("name", ["fold2bit_c2_dram.txt", "fold_f32_c1_dram.txt"])
+def test_traffic_only_while_the_source_matches(tmp_path, monkeypatch, name):
     """A summary stamped with the kernel source's sha256 yields its DRAM bytes; any change to the source
     withdraws them (the committed summary is checked against the committed source the same way)."""
     import hashlib
 
-    summary = open(os.path.join(bench.ROOT, "profiles", "fold2bit_c2_dram.txt")).read()
+    summary = open(os.path.join(bench.ROOT, "profiles", name)).read()
     recorded = int(summary.split("dram_bytes_per_launch=")[1].split()[0])
     root = tmp_path / "repo"
     shutil.copytree(os.path.join(bench.ROOT, "profiles"), root / "profiles")
@@ -42,12 +45,12 @@ def test_traffic_only_while_the_source_matches(tmp_path, monkeypatch):
     shutil.copy(os.path.join(bench.ROOT, "paper_2501_05993_gb300", "csrc", "fold_bulk.cu"), csrc / "fold_bulk.cu")
     sha = hashlib.sha256((csrc / "fold_bulk.cu").read_bytes()).hexdigest()
     lines = [f"source_sha256={sha}" if l.startswith("source_sha256=") else l for l in summary.splitlines()]
-    (root / "profiles" / "fold2bit_c2_dram.txt").write_text("\n".join(lines) + "\n")
+    (root / "profiles" / name).write_text("\n".join(lines) + "\n")
     monkeypatch.setattr(bench, "ROOT", str(root))
-    assert bench.read_traffic("fold_bulk.cu") == recorded  # same source: the recorded figure
+    assert bench.read_traffic("fold_bulk.cu", name) == recorded  # same source: the recorded figure
     with open(csrc / "fold_bulk.cu", "a") as f:
         f.write("\n// changed\n")
-    assert bench.read_traffic("fold_bulk.cu") is None
+    assert bench.read_traffic("fold_bulk.cu", name) is None
 
 
 def test_clock_sampler_stop_reads_and_removes_its_file(tmp_path):
