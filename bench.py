@@ -762,7 +762,7 @@ def run_batch(args, emit=True):
                        "samples_per_step": total_samples, "bytes_per_step": total_bytes,
                        "max_L": max(int(g.L) for g in batch.geometry), "schedule": chosen,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "l2": f"{total_bytes >> 30} GB of inputs per step > L2",
+                       "l2": f"{total_bytes / 1e9:.2f} GB of inputs per step > L2",
                        "fold_ms": fold_ms, "batched_vs_plain_max_phasor_diff": worst,
                        "finalize_ms_by_dft": fin_modes},
             "plain": {"value": world * total_samples / (plain_ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": plain_ms,
@@ -965,6 +965,9 @@ def run_serve(args, emit=True):
     srv = pcal.Server(args.serve_budget_gb << 30, len(streams), period_s, 0.1)
     ids = [srv.open(st["fs"], st["fc"], st["fo"], st["fmt"]) for st in streams]
     rng = np.random.default_rng(SERVE_SEED + 1)
+    # the clock sampler starts here, so that nvidia-smi's own start-up is over before the real-time phase
+    clocks = ClockSampler(dev)
+    clocks.start()
     t_adm = time.perf_counter()  # every stream admitted (its memory carved) before the clock starts
     while srv.stats()["admitted"] < len(streams) and time.perf_counter() - t_adm < 30:
         time.sleep(0.001)
@@ -981,8 +984,6 @@ def run_serve(args, emit=True):
     # together every tick, each stamped with its scheduled arrival time, so a period's latency runs from
     # the arrival of its last chunk (through any submit lag, the copy, the fold and the finalize) to its
     # results on the host
-    clocks = ClockSampler(dev)
-    clocks.start()
     import gc
 
     gc.collect()
