@@ -39,6 +39,7 @@ FS, FC, FO, N_TONES = 64_000_000, 1_000_000, 10_000, 64
 AMP, TD = 0.01, 12.5e-9
 M = 512_000_000
 N_BUFFERS = 8
+KERNEL_LAUNCHES = 100  # back-to-back launches of the dominant kernel timed alone
 SEED = 2501059932
 WORKLOAD = "2-bit single channel, fs=64 MHz, f_comb=1 MHz (N=64), f_offset=10 kHz (L=6400), 512M samples (128 MB)"
 METRIC = "PCal Gsamples/s (2-bit single-stream extraction: accumulate + finalize)"
@@ -402,19 +403,21 @@ def run_gpu(args):
     res = plan.results()  # the last timed step's phasors and delay
     # the dominant kernel alone: K back-to-back fold launches on the same
     # stream (CUDA events around them), then K finalize launches
+    # (at least KERNEL_LAUNCHES of each: a loop pays ~40 us once to fill and drain, 2 us per launch at K = 20)
     f0, f1, f2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    nk = max(args.steps, KERNEL_LAUNCHES)
     launches_f = plan.stats()["kernel_launches"]
     f0.record(stream)
-    for k in range(args.steps):
+    for k in range(nk):
         pcal.pcal_accumulate(h, bufs[k % N_BUFFERS], M, stream)
     f1.record(stream)
-    for k in range(args.steps):
+    for k in range(nk):
         pcal.pcal_finalize_device(h, stream)
     f2.record(stream)
     torch.cuda.synchronize()
-    fold_launches = plan.stats()["kernel_launches"] - launches_f - args.steps
-    fold_ms = f0.elapsed_time(f1) / args.steps
-    fin_ms = f1.elapsed_time(f2) / args.steps
+    fold_launches = plan.stats()["kernel_launches"] - launches_f - nk
+    fold_ms = f0.elapsed_time(f1) / nk
+    fin_ms = f1.elapsed_time(f2) / nk
     total_ms = reduce_max(total_ms, dist, "cuda")
     value = aggregate_value(world, M, args.steps, total_ms)
 
@@ -485,8 +488,8 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": f"inputs rotate over {N_BUFFERS} device buffers ({N_BUFFERS * nbytes >> 20} MB) > L2",
-                       "fold_ms": fold_ms, "finalize_ms": fin_ms, "fold_launches_per_step": fold_launches / args.steps,
-                       "kernel_timing": "fold and finalize each timed over K back-to-back launches after the timed region", "td_s": res["td"], "sigma_td_s": res["sigma_td"],
+                       "fold_ms": fold_ms, "finalize_ms": fin_ms, "fold_launches_per_step": fold_launches / nk,
+                       "kernel_timing": f"fold and finalize each timed over max(K, {KERNEL_LAUNCHES}) = {nk} back-to-back launches after the timed region", "td_s": res["td"], "sigma_td_s": res["sigma_td"],
                        "td_injected_s": TD},
             "roofline": roofline, "cpu_baseline": cpu, "cpu_fold_baseline": cpu_fold, "e2e": e2e, "clocks": clk,
             "gpu_launches": launches,
@@ -812,7 +815,7 @@ def run_c1(args, emit=True, n_buffers=8):
         if i % 64 == 0:
             torch.cuda.synchronize()
     torch.cuda.synchronize()
-    k = max(args.steps, 20)
+    k = max(args.steps, KERNEL_LAUNCHES)  # an extra line: its own K, long enough that fill and drain do not count
     e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     e[0].record(stream)
     for i in range(k):
