@@ -382,11 +382,12 @@ def run_gpu(args):
         i += 1
         if i % 64 == 0:
             torch.cuda.synchronize()
-    torch.cuda.synchronize()
-    barrier()
-
+    # host work before the bracket: an idle GPU's first kernel runs slower (a C2 fold after 1 ms idle took
+    # 13-17 us longer, after 100 ms 40 us longer), so the first launch follows the synchronisation at once
     launches0 = plan.stats()["kernel_launches"]
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier()
     torch.cuda.synchronize()
     # timed region: K whole steps; events only at its ends, so that each
     # kernel can launch as a programmatic dependent of the one before it

@@ -297,13 +297,15 @@ int pcal_tones_from_counts_noalloc(double fs, double f_comb, double f_offset, in
  * A batch holds up to PCAL_MAX_BATCH channels (2-bit or int8 samples), each
  * with its own fs, f_comb, f_offset and N, hence its own period L (Eq. 4).
  * One pcal_batch_accumulate call folds a run of samples of every channel with
- * ONE persistent kernel launch over a work list of all channels' tiles (plus
- * one small launch for ragged heads and tails, and one that advances the
- * channels' sample indices); pcal_batch_finalize_device turns every
- * channel's bins into its N phasors, amplitude, phase and delay (Sec. 2) with
- * one launch, a thread-block cluster per channel.  The bins are exact
- * integers, so a channel's counts and phasors do not depend on the batch it
- * is folded in or on the schedule.  The paper processes one stream at a
+ * ONE persistent kernel launch over a work list of all channels' tiles; the
+ * same launch folds the ragged heads and tails (pieces of at most 8 KB) and
+ * its last CTA advances the channels' sample indices.  A call that repeats
+ * the buffers and lengths of an earlier call on the same stream reuses that
+ * call's device descriptors without a copy.  pcal_batch_finalize_device
+ * turns every channel's bins into its N phasors, amplitude, phase and delay
+ * (Sec. 2) with one launch, a thread-block cluster per channel.  The bins
+ * are exact integers, so a channel's counts and phasors do not depend on the
+ * batch it is folded in or on the schedule.  The paper processes one stream at a
  * time; batching is an interface choice of this library.
  */
 #define PCAL_MAX_BATCH 4096   /* channels per batch                           */
