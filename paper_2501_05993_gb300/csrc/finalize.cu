@@ -959,8 +959,17 @@ __global__ void __launch_bounds__(kClusterThreads) batch_fin_kernel(BatchChan* c
     const int i = (int)(blockIdx.x / cg::this_cluster().num_blocks());
     const int c = list ? list[i] : i;
     BatchChan& bc = ch[c];
-    FinArgs a = batch_fin_args(bc);
-    if (split) a.Pout = bc.Pslot;
+    // The arguments live in shared memory: a per-thread copy passed by
+    // reference to the out-of-line products went to each thread's stack, and
+    // those stores (376 B x 256 threads x 16 CTAs per channel, ~88 MB for 64
+    // channels) left dirty L2 lines that the next fold had to write back
+    // (+50 us per C3 step).
+    __shared__ FinArgs a;
+    if (threadIdx.x == 0) {
+        a = batch_fin_args(bc);
+        if (split) a.Pout = bc.Pslot;
+    }
+    __syncthreads();
     // every CTA has read the state above before the first cluster barrier
     // inside, and rank 0 returns after the last one
     if (cluster_finalize(a) && threadIdx.x == 0) bc.period_start = bc.n_abs;
@@ -970,7 +979,9 @@ __global__ void __launch_bounds__(kClusterThreads) batch_fin_kernel(BatchChan* c
 // post-processing from its tone and P slots and starts its next period.
 __global__ void __launch_bounds__(kClusterThreads) batch_products_kernel(BatchChan* ch) {
     BatchChan& bc = ch[blockIdx.x];
-    const FinArgs a = batch_fin_args(bc);
+    __shared__ FinArgs a;  // in shared memory, not on every thread's stack
+    if (threadIdx.x == 0) a = batch_fin_args(bc);
+    __syncthreads();
     extern __shared__ __align__(16) uint8_t dsm[];
     const ClusterSmem sm = cluster_layout(dsm, bc.N);
     const int t = threadIdx.x;
@@ -1254,7 +1265,11 @@ cudaError_t launch_batch_products(BatchChan* d_ch, int n_ch, int max_n, cudaStre
 // CUDA calls that a stream capture does not allow).  max_n: the largest N of
 // the batch's channels.
 cudaError_t launch_batch_finalize(BatchChan* d_ch, int n_ch, int max_n, const int* d_list, cudaStream_t s, int split) {
-    const int C = cluster_size_for_device();
+    // 8-CTA clusters: with one cluster per channel the launch is several waves
+    // of CTAs, and fewer, longer clusters finish sooner (64 channels of up to
+    // L 25600: 16 CTAs 53 us, 8 CTAs 43 us, 4 CTAs 57 us; same phasors)
+    int C = cluster_size_for_device();
+    if (C > 8) C = 8;
     if (C == 0) return cudaErrorNotSupported;
     if (max_n > kClusterBigN) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
