@@ -527,7 +527,11 @@ struct PendingArgs {
     int n;
 };
 
-__global__ void __launch_bounds__(32 * kReduceWarps) reduce_f32_kernel(const PendingArgs pa, int cols_total,
+// The slot arguments are indexed at run time: as a grid constant they are
+// read in place (a by-value parameter was copied to every thread's stack,
+// 104 B x 512 threads per block: megabytes of dirty L2 lines per flush that
+// the next fold had to write back).
+__global__ void __launch_bounds__(32 * kReduceWarps) reduce_f32_kernel(const __grid_constant__ PendingArgs pa, int cols_total,
                                                                       int64_t L, float2* __restrict__ acc) {
     allow_dependents();
     grid_dependency_wait();

@@ -66,7 +66,7 @@ __device__ __forceinline__ df sample_df(const RotAccArgs& a, int64_t i) {
     return a.lev[c];
 }
 
-__global__ void rotplan_acc_kernel(RotAccArgs a) {
+__global__ void rotplan_acc_kernel(const __grid_constant__ RotAccArgs a) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= (int64_t)a.N * a.lanes) return;
     const int b = (int)(t % a.N), lane = (int)(t / a.N);
