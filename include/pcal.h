@@ -591,10 +591,12 @@ int pcal_rotplan_read_results(pcal_rotplan* plan, double* phasors, double* amp, 
  * operand workspace grows (cudaMalloc) when C exceeds every earlier call's.
  * pcal_dft_check synchronises and returns PCAL_ETIMEOUT (with the device
  * error bits) if a bounded wait inside the kernel gave up.
+ * A tile is 128 channels x 256 output columns (TF32x3) or x 128 (BF16x6).
  * pcal_dft_weights_host writes weight tile (tile, chunk) of a tensor-core
- * mode into `parts` (HOST, 3 x 16 KB: part p at byte 16384 p; rows = the
- * tile's output columns, at most 128, returned in *rows; the mode's number
- * of parts, 2 or 3, in *n_parts); host-only, for tests of the layout.
+ * mode into `parts` (HOST, 3 x W x 128 bytes, W = the mode's tile width:
+ * part p at byte W * 128 * p; rows = the tile's output columns, at most W,
+ * returned in *rows; the mode's number of parts, 2 or 3, in *n_parts);
+ * host-only, for tests of the layout.
  */
 #define PCAL_DFT_FP32 0
 #define PCAL_DFT_TC_TF32X3 1

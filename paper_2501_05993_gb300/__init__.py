@@ -882,6 +882,7 @@ class RotPlan:
 
 PCAL_DFT_FP32, PCAL_DFT_TC_TF32X3, PCAL_DFT_TC_BF16X6 = 0, 1, 2
 DFT_MODES = {"fp32": PCAL_DFT_FP32, "tf32x3": PCAL_DFT_TC_TF32X3, "bf16x6": PCAL_DFT_TC_BF16X6}
+DFT_TILE_COLS = {"tf32x3": 256, "bf16x6": 128}  # output columns per weight tile (pcal.h)
 
 
 class Dft:
@@ -928,13 +929,14 @@ class Dft:
 
 
 def pcal_dft_weights_host(N: int, mode: str, tile: int, chunk: int) -> tuple[list, int]:
-    """Host copy of weight tile (tile, chunk) of a tensor-core mode: its parts (2 or 3 byte arrays of 16 KB,
-    the tile image of each part) and its rows."""
-    buf = np.zeros(3 * 16384, np.uint8)
+    """Host copy of weight tile (tile, chunk) of a tensor-core mode: its parts (2 or 3 byte arrays of
+    DFT_TILE_COLS[mode] x 128 bytes, the tile image of each part) and its rows."""
+    stride = DFT_TILE_COLS.get(mode, 128) * 128
+    buf = np.zeros(3 * stride, np.uint8)
     rows, n_parts = ctypes.c_int(), ctypes.c_int()
     _check(load().pcal_dft_weights_host(int(N), DFT_MODES[mode], int(tile), int(chunk), buf.ctypes.data,
                                         ctypes.byref(rows), ctypes.byref(n_parts)), "pcal_dft_weights_host")
-    return [buf[16384 * p:16384 * (p + 1)] for p in range(n_parts.value)], rows.value
+    return [buf[stride * p:stride * (p + 1)] for p in range(n_parts.value)], rows.value
 
 
 def pcal_selftest_wait_timeout(limit_s: float) -> tuple[int, int]:

@@ -56,22 +56,28 @@ constexpr int kATile = kTcM * kChunkBytes;      // 16 KB: one part of a row tile
 constexpr int kTcThreads = 384;                 // 12 warps
 constexpr int kDrainWarp0 = 4;                  // warps 4..11 drain the accumulators
 constexpr int kDrainWarps = 8;
-constexpr int kAccCols = 128;                   // TMEM columns of one accumulator buffer
-constexpr int kTmemCols = 2 * kAccCols;         // two buffers (a power of two)
 
-// Per mode: parts per operand, products per K-step and pipeline depth.  Both
-// modes take 128-column tiles; split TF32 moves 64 KB per chunk (3 stages),
-// split BF16 96 KB (2 stages): 192 KB of shared memory, one CTA per SM.
+// Per mode: parts per operand, products per K-step, tile width and pipeline
+// depth.  The MMAs read their operands from shared memory, and with
+// 128 x 128 tiles those reads plus the copies filling the stages need more
+// shared-memory bandwidth than an SM has (split TF32 at its peak: ~109 B per
+// clock of operand reads and ~73 B of fills against 128 B), which held the
+// tensor pipe near 50-65 %.  Split TF32 therefore takes 128 x 256 tiles
+// (each A byte feeds twice the columns: ~82 + 53 B per clock) with two
+// 96 KB stages; split BF16 keeps 128 x 128 tiles (a 256-column stage of
+// three parts would be 144 KB).  192 KB of shared memory, one CTA per SM.
 template <int MODE>
 struct TcCfg {
     static constexpr bool kTf32 = MODE == PCAL_DFT_TC_TF32X3;
     static constexpr int kParts = kTf32 ? 2 : 3;
     static constexpr int kProducts = kTf32 ? 3 : 6;
-    static constexpr int kNT = 128;                                  // output columns per tile
-    static constexpr int kBTile = kNT * kChunkBytes;                 // 16 KB: one weight part per chunk
+    static constexpr int kNT = kTf32 ? 256 : 128;                    // output columns per tile
+    static constexpr int kBTile = kNT * kChunkBytes;                 // one weight part per chunk
     static constexpr int kStageBytes = kParts * (kATile + kBTile);
-    static constexpr int kStages = kTf32 ? 3 : 2;
+    static constexpr int kStages = 2;
     static constexpr int kSmem = kStages * kStageBytes;
+    static constexpr int kAccCols = kNT;                             // TMEM columns of one accumulator buffer
+    static constexpr int kTmemCols = 2 * kAccCols;                   // two buffers (a power of two)
 };
 
 // The products of a K-step as (part of A, part of B), the small cross
@@ -360,7 +366,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) dft_tc_kernel(const DftTcArgs a
     constexpr int KC = kChunkBytes / ES;  // K values per chunk
     constexpr int KS = 32 / ES;           // K values per MMA
     constexpr int NP = Cfg::kParts, kStages = Cfg::kStages, kStageBytes = Cfg::kStageBytes;
+    constexpr int kAccCols = Cfg::kAccCols, kTmemCols = Cfg::kTmemCols;
     constexpr int kDrainCols = kAccCols / 2;  // columns per drain warp
+    constexpr int kPieces = kDrainCols / 32;  // 32-column TMEM loads per drain warp
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages], acc_full[2], acc_empty[2], done;
     __shared__ uint32_t s_tmem;
@@ -458,7 +466,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) dft_tc_kernel(const DftTcArgs a
         const int q = warp & 3;                                   // TMEM lane quadrant of this warp
         const int c0 = ((warp - kDrainWarp0) >> 2) * kDrainCols;  // first column of this warp
         const uint32_t lane_addr = (uint32_t)(32 * q) << 16;
-        const int pieces = nt > c0 ? (nt - c0 >= kDrainCols ? 2 : (nt - c0 + 31) / 32) : 0;  // 32-column loads
+        const int pieces = nt > c0 ? (nt - c0 >= kDrainCols ? kPieces : (nt - c0 + 31) / 32) : 0;  // 32-column loads
         float sum[kDrainCols];
 #pragma unroll
         for (int j = 0; j < kDrainCols; ++j) sum[j] = 0.f;
@@ -473,15 +481,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) dft_tc_kernel(const DftTcArgs a
             tc_fence_after();
             const uint32_t base = tmem + lane_addr + (uint32_t)(b * kAccCols + c0);
             uint32_t v[32];
-            if (pieces > 0) {
-                tc_ld32(base, v);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) sum[j] += __uint_as_float(v[j]);
-            }
-            if (pieces > 1) {
-                tc_ld32(base + 32u, v);
+            for (int pc = 0; pc < kPieces; ++pc) {
+                if (pc < pieces) {
+                    tc_ld32(base + 32u * pc, v);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) sum[32 + j] += __uint_as_float(v[j]);
+                    for (int j = 0; j < 32; ++j) sum[32 * pc + j] += __uint_as_float(v[j]);
+                }
             }
             tc_fence_before();
             __syncwarp();
@@ -565,9 +571,10 @@ struct pcal_dft {
 
 namespace {
 
-constexpr int kTileCols = 128;  // output columns per tile, either mode
-static_assert(TcCfg<PCAL_DFT_TC_TF32X3>::kNT == kTileCols && TcCfg<PCAL_DFT_TC_BF16X6>::kNT == kTileCols,
-              "one tile width");
+// output columns per tile of a tensor-core mode
+inline int tile_cols(int mode) {
+    return mode == PCAL_DFT_TC_TF32X3 ? TcCfg<PCAL_DFT_TC_TF32X3>::kNT : TcCfg<PCAL_DFT_TC_BF16X6>::kNT;
+}
 
 inline int parts_of(int mode) {
     return mode == PCAL_DFT_TC_TF32X3 ? TcCfg<PCAL_DFT_TC_TF32X3>::kParts : TcCfg<PCAL_DFT_TC_BF16X6>::kParts;
@@ -579,8 +586,9 @@ inline int parts_of(int mode) {
 int build_weight_tile(int N, int mode, int t, int kc, const double* twr, const double* twi, uint8_t* out,
                       size_t part_stride) {
     const int n_cols = (2 * N + 15) / 16 * 16;
-    const int n0 = t * kTileCols;
-    const int nt = n_cols - n0 < kTileCols ? n_cols - n0 : kTileCols;
+    const int tc = tile_cols(mode);
+    const int n0 = t * tc;
+    const int nt = n_cols - n0 < tc ? n_cols - n0 : tc;
     const int es = mode == PCAL_DFT_TC_TF32X3 ? 4 : 2;
     const int kcv = kChunkBytes / es;
     const int np = parts_of(mode);
@@ -618,12 +626,12 @@ extern "C" int pcal_dft_weights_host(int N, int mode, int tile, int chunk, void*
     const int n_cols = (2 * N + 15) / 16 * 16;
     const int es = mode == PCAL_DFT_TC_TF32X3 ? 4 : 2;
     const int k_chunks = (2 * N + kChunkBytes / es - 1) / (kChunkBytes / es);
-    if (tile < 0 || tile * kTileCols >= n_cols || chunk < 0 || chunk >= k_chunks) return PCAL_EINVAL;
+    if (tile < 0 || tile * tile_cols(mode) >= n_cols || chunk < 0 || chunk >= k_chunks) return PCAL_EINVAL;
     double* tw = new (std::nothrow) double[2 * (size_t)N];
     if (!tw) return PCAL_ENOMEM;
     twiddles(N, tw, tw + N);
     *rows = build_weight_tile(N, mode, tile, chunk, tw, tw + N, static_cast<uint8_t*>(parts),
-                              (size_t)kTileCols * kChunkBytes);
+                              (size_t)tile_cols(mode) * kChunkBytes);
     *n_parts = parts_of(mode);
     delete[] tw;
     return PCAL_OK;
@@ -638,7 +646,8 @@ extern "C" int pcal_dft_create(int N, int mode, pcal_dft** out) {
     d->N = N;
     d->mode = mode;
     d->n_cols = (2 * N + 15) / 16 * 16;
-    d->col_tiles = mode == PCAL_DFT_FP32 ? 0 : (d->n_cols + kTileCols - 1) / kTileCols;
+    const int tc = mode == PCAL_DFT_FP32 ? 0 : tile_cols(mode);
+    d->col_tiles = mode == PCAL_DFT_FP32 ? 0 : (d->n_cols + tc - 1) / tc;
     d->parts = mode == PCAL_DFT_FP32 ? 0 : parts_of(mode);
     const int es = mode == PCAL_DFT_TC_TF32X3 ? 4 : 2;
     d->k_chunks = (2 * N + kChunkBytes / es - 1) / (kChunkBytes / es);
@@ -660,12 +669,12 @@ extern "C" int pcal_dft_create(int N, int mode, pcal_dft** out) {
     } else if (e == cudaSuccess) {
         // per (column tile, chunk): the parts of the tile's rows, one after the
         // other (a ragged last tile keeps its rows together): one copy per chunk
-        const size_t block = (size_t)d->parts * kTileCols * kChunkBytes;
+        const size_t block = (size_t)d->parts * tc * kChunkBytes;
         const size_t bytes = (size_t)d->col_tiles * d->k_chunks * block;
         uint8_t* h = new (std::nothrow) uint8_t[bytes];
         if (!h) e = cudaErrorMemoryAllocation;
         for (int t = 0; h && t < d->col_tiles; ++t) {
-            const int nt = d->n_cols - t * kTileCols < kTileCols ? d->n_cols - t * kTileCols : kTileCols;
+            const int nt = d->n_cols - t * tc < tc ? d->n_cols - t * tc : tc;
             for (int kc = 0; kc < d->k_chunks; ++kc)
                 build_weight_tile(N, mode, t, kc, tw, tw + N, h + ((size_t)t * d->k_chunks + kc) * block,
                                   (size_t)nt * kChunkBytes);

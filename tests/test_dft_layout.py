@@ -19,7 +19,7 @@ import paper_2501_05993_gb300 as pcal
 
 ESIZE = {"tf32x3": 4, "bf16x6": 2}
 PARTS = {"tf32x3": 2, "bf16x6": 3}
-TILE = 128  # output columns per tile
+TILE = {"tf32x3": 256, "bf16x6": 128}  # output columns per tile
 
 
 @pytest.fixture(scope="module")
@@ -62,7 +62,8 @@ def test_weight_tiles_decode_to_the_dft_matrix(lib, mode, N):
     es = ESIZE[mode]
     kcv = 128 // es
     n_cols = (2 * N + 15) // 16 * 16
-    tiles = (n_cols + TILE - 1) // TILE
+    tile = TILE[mode]
+    tiles = (n_cols + tile - 1) // tile
     chunks = (2 * N + kcv - 1) // kcv
     # the sum of the parts carries the float32-rounded weight: 2^-22 of it left out by two TF32 parts, 2^-26 by
     # three BF16 parts, plus the float32 rounding (2^-24)
@@ -71,9 +72,9 @@ def test_weight_tiles_decode_to_the_dft_matrix(lib, mode, N):
         for c in sorted({0, chunks // 2, chunks - 1}):
             parts, rows = pcal.pcal_dft_weights_host(N, mode, t, c)
             assert len(parts) == PARTS[mode]
-            assert rows == min(TILE, n_cols - TILE * t) and rows % 16 == 0
+            assert rows == min(tile, n_cols - tile * t) and rows % 16 == 0
             vals = [decode(p, rows, es) for p in parts]
-            n = TILE * t + np.arange(rows)[:, None]
+            n = tile * t + np.arange(rows)[:, None]
             k = c * kcv + np.arange(kcv)[None, :]
             w = expected(N, n, k)
             assert np.max(np.abs(sum(vals) - w)) <= tol, (t, c)
