@@ -578,7 +578,7 @@ int pcal_rotplan_read_results(pcal_rotplan* plan, double* phasors, double* amp, 
  *                       parts (x = h + l), three products
  *   PCAL_DFT_TC_BF16X6  the same with three BF16 parts (x = h + m + l) and
  *                       the six products of total order <= 2
- * In both tensor-core modes every K chunk of 128 bytes per row starts a fresh
+ * In both tensor-core modes every K chunk (32 values per row) starts a fresh
  * FP32 accumulator in tensor memory, which is added into FP32 registers on
  * CUDA cores (round to nearest) while the next chunk accumulates: the error
  * stays at the level of an FP32 sum.  Errors vs FP64 at C = 4096, N = 1024,
@@ -591,10 +591,11 @@ int pcal_rotplan_read_results(pcal_rotplan* plan, double* phasors, double* amp, 
  * operand workspace grows (cudaMalloc) when C exceeds every earlier call's.
  * pcal_dft_check synchronises and returns PCAL_ETIMEOUT (with the device
  * error bits) if a bounded wait inside the kernel gave up.
- * A tile is 128 channels x 256 output columns (TF32x3) or x 128 (BF16x6).
+ * A tile is 128 channels x 256 output columns; K goes in chunks of 128
+ * bytes per row (TF32x3: 32 values) or 64 bytes (BF16x6: 32 values).
  * pcal_dft_weights_host writes weight tile (tile, chunk) of a tensor-core
- * mode into `parts` (HOST, 3 x W x 128 bytes, W = the mode's tile width:
- * part p at byte W * 128 * p; rows = the tile's output columns, at most W,
+ * mode into `parts` (HOST, 3 x 256 x B bytes, B = the mode's chunk bytes:
+ * part p at byte 256 * B * p; rows = the tile's output columns, at most 256,
  * returned in *rows; the mode's number of parts, 2 or 3, in *n_parts);
  * host-only, for tests of the layout.
  */

@@ -882,7 +882,8 @@ class RotPlan:
 
 PCAL_DFT_FP32, PCAL_DFT_TC_TF32X3, PCAL_DFT_TC_BF16X6 = 0, 1, 2
 DFT_MODES = {"fp32": PCAL_DFT_FP32, "tf32x3": PCAL_DFT_TC_TF32X3, "bf16x6": PCAL_DFT_TC_BF16X6}
-DFT_TILE_COLS = {"tf32x3": 256, "bf16x6": 128}  # output columns per weight tile (pcal.h)
+DFT_TILE_COLS = {"tf32x3": 256, "bf16x6": 256}  # output columns per weight tile (pcal.h)
+DFT_CHUNK_BYTES = {"tf32x3": 128, "bf16x6": 64}  # bytes of K per weight tile row (pcal.h)
 
 
 class Dft:
@@ -930,8 +931,8 @@ class Dft:
 
 def pcal_dft_weights_host(N: int, mode: str, tile: int, chunk: int) -> tuple[list, int]:
     """Host copy of weight tile (tile, chunk) of a tensor-core mode: its parts (2 or 3 byte arrays of
-    DFT_TILE_COLS[mode] x 128 bytes, the tile image of each part) and its rows."""
-    stride = DFT_TILE_COLS.get(mode, 128) * 128
+    DFT_TILE_COLS[mode] x DFT_CHUNK_BYTES[mode] bytes, the tile image of each part) and its rows."""
+    stride = DFT_TILE_COLS.get(mode, 128) * DFT_CHUNK_BYTES.get(mode, 128)
     buf = np.zeros(3 * stride, np.uint8)
     rows, n_parts = ctypes.c_int(), ctypes.c_int()
     _check(load().pcal_dft_weights_host(int(N), DFT_MODES[mode], int(tile), int(chunk), buf.ctypes.data,

@@ -51,8 +51,6 @@ namespace {
 using namespace pcal_ptx;
 
 constexpr int kTcM = 128;                       // channels per tile (MMA M)
-constexpr int kChunkBytes = 128;                // bytes of K per row and chunk
-constexpr int kATile = kTcM * kChunkBytes;      // 16 KB: one part of a row tile's chunk
 constexpr int kTcThreads = 384;                 // 12 warps
 constexpr int kDrainWarp0 = 4;                  // warps 4..11 drain the accumulators
 constexpr int kDrainWarps = 8;
@@ -62,19 +60,22 @@ constexpr int kDrainWarps = 8;
 // 128 x 128 tiles those reads plus the copies filling the stages need more
 // shared-memory bandwidth than an SM has (split TF32 at its peak: ~109 B per
 // clock of operand reads and ~73 B of fills against 128 B), which held the
-// tensor pipe near 50-65 %.  Split TF32 therefore takes 128 x 256 tiles
-// (each A byte feeds twice the columns: ~82 + 53 B per clock) with two
-// 96 KB stages; split BF16 keeps 128 x 128 tiles (a 256-column stage of
-// three parts would be 144 KB).  192 KB of shared memory, one CTA per SM.
+// tensor pipe near 50-65 %.  Both modes therefore take 128 x 256 tiles (each
+// A byte feeds twice the columns).  Split TF32: K chunks of 128 bytes per
+// row, two 96 KB stages; split BF16 (three parts): K chunks of 64 bytes, three
+// 72 KB stages.  192 / 216 KB of shared memory, one CTA per SM.
 template <int MODE>
 struct TcCfg {
     static constexpr bool kTf32 = MODE == PCAL_DFT_TC_TF32X3;
     static constexpr int kParts = kTf32 ? 2 : 3;
     static constexpr int kProducts = kTf32 ? 3 : 6;
-    static constexpr int kNT = kTf32 ? 256 : 128;                    // output columns per tile
-    static constexpr int kBTile = kNT * kChunkBytes;                 // one weight part per chunk
+    static constexpr int kChunk = kTf32 ? 128 : 64;                  // bytes of K per row and chunk
+    static constexpr int kATile = kTcM * kChunk;                     // one part of a row tile's chunk
+    static constexpr int kImageWords = kATile / 16;                  // 16-byte words of one tile image
+    static constexpr int kNT = 256;                                  // output columns per tile
+    static constexpr int kBTile = kNT * kChunk;                      // one weight part per chunk
     static constexpr int kStageBytes = kParts * (kATile + kBTile);
-    static constexpr int kStages = 2;
+    static constexpr int kStages = kTf32 ? 2 : 3;
     static constexpr int kSmem = kStages * kStageBytes;
     static constexpr int kAccCols = kNT;                             // TMEM columns of one accumulator buffer
     static constexpr int kTmemCols = 2 * kAccCols;                   // two buffers (a power of two)
@@ -258,7 +259,7 @@ struct DftTcArgs {
     int N;
     int n_cols;        // 2N rounded up to 16
     int k_chunks;      // chunks of K = 2N
-    const uint8_t* a;  // operand tiles of P: [row tile][chunk] x parts x kATile bytes
+    const uint8_t* a;  // operand tiles of P: [row tile][chunk] x parts x kATile bytes (per mode)
     const uint8_t* w;  // weight tiles: [column tile][chunk] x parts x (tile rows x 128) bytes
     unsigned int* err;
 };
@@ -269,13 +270,12 @@ struct DftTcArgs {
 // r's K values g*V .. g*V+V-1 of the chunk (V = 16 / element size: one core-
 // matrix row), so a thread per word reads V consecutive values of one row of
 // P (whole sectors) and writes that word of every part.
-constexpr int kImageWords = kATile / 16;  // 16-byte words of one tile image
 
 template <int MODE>
 __host__ __device__ inline void split_word(const float2* __restrict__ P, int64_t C, int N, int k_chunks,
                                            int64_t blk, int w, uint4* out) {
     constexpr int ES = esize_of<MODE>();
-    constexpr int KC = kChunkBytes / ES;
+    constexpr int KC = TcCfg<MODE>::kChunk / ES;
     constexpr int V = 16 / ES;
     constexpr int NP = TcCfg<MODE>::kParts;
     const int r = w % kTcM, g = w / kTcM;
@@ -331,7 +331,7 @@ __host__ __device__ inline void split_word(const float2* __restrict__ P, int64_t
 // keeps one row per thread.
 template <int MODE>
 __host__ __device__ inline int split_word_of_thread(int e) {
-    constexpr int kRowWords = kChunkBytes / 16;  // words of one row of a chunk
+    constexpr int kRowWords = TcCfg<MODE>::kChunk / 16;  // words of one row of a chunk
     return MODE == PCAL_DFT_TC_BF16X6 ? (e % kRowWords) * kTcM + e / kRowWords : e;
 }
 
@@ -339,6 +339,7 @@ template <int MODE>
 __global__ void __launch_bounds__(256) split_p_kernel(const float2* __restrict__ P, int64_t C, int N, int k_chunks,
                                                       uint4* __restrict__ out, int64_t words) {
     constexpr int NP = TcCfg<MODE>::kParts;
+    constexpr int kImageWords = TcCfg<MODE>::kImageWords;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += stride) {
         const int64_t blk = i / kImageWords;
@@ -363,7 +364,8 @@ template <int MODE>
 __global__ void __launch_bounds__(kTcThreads, 1) dft_tc_kernel(const DftTcArgs a) {
     using Cfg = TcCfg<MODE>;
     constexpr int ES = esize_of<MODE>();
-    constexpr int KC = kChunkBytes / ES;  // K values per chunk
+    constexpr int kATile = Cfg::kATile;
+    constexpr int KC = Cfg::kChunk / ES;  // K values per chunk
     constexpr int KS = 32 / ES;           // K values per MMA
     constexpr int NP = Cfg::kParts, kStages = Cfg::kStages, kStageBytes = Cfg::kStageBytes;
     constexpr int kAccCols = Cfg::kAccCols, kTmemCols = Cfg::kTmemCols;
@@ -378,7 +380,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) dft_tc_kernel(const DftTcArgs a
     const int64_t m0 = mt * kTcM;
     const int n0 = blockIdx.y * Cfg::kNT;
     const int nt = a.n_cols - n0 < Cfg::kNT ? a.n_cols - n0 : Cfg::kNT;  // a multiple of 16
-    const uint32_t w_bytes = (uint32_t)nt * kChunkBytes;                 // one weight part of a chunk
+    const uint32_t w_bytes = (uint32_t)nt * Cfg::kChunk;                 // one weight part of a chunk
     if (warp == 2) {
         tc_alloc(&s_tmem, kTmemCols);
         tc_relinquish();
@@ -580,8 +582,13 @@ inline int parts_of(int mode) {
     return mode == PCAL_DFT_TC_TF32X3 ? TcCfg<PCAL_DFT_TC_TF32X3>::kParts : TcCfg<PCAL_DFT_TC_BF16X6>::kParts;
 }
 
+// bytes of K per row and chunk of a tensor-core mode
+inline int chunk_bytes(int mode) {
+    return mode == PCAL_DFT_TC_TF32X3 ? TcCfg<PCAL_DFT_TC_TF32X3>::kChunk : TcCfg<PCAL_DFT_TC_BF16X6>::kChunk;
+}
+
 // Weight tile of column tile t, chunk kc, in the shared-memory image the
-// kernel copies (rows = the tile's columns, 128 bytes of K per row): part p
+// kernel copies (rows = the tile's columns, the mode's chunk of K per row): part p
 // at out + p * part_stride.  Returns the tile's rows.
 int build_weight_tile(int N, int mode, int t, int kc, const double* twr, const double* twi, uint8_t* out,
                       size_t part_stride) {
@@ -590,10 +597,10 @@ int build_weight_tile(int N, int mode, int t, int kc, const double* twr, const d
     const int n0 = t * tc;
     const int nt = n_cols - n0 < tc ? n_cols - n0 : tc;
     const int es = mode == PCAL_DFT_TC_TF32X3 ? 4 : 2;
-    const int kcv = kChunkBytes / es;
+    const int kcv = chunk_bytes(mode) / es;
     const int np = parts_of(mode);
     uint8_t* parts[3] = {out, out + part_stride, out + 2 * part_stride};
-    for (int p = 0; p < np; ++p) memset(parts[p], 0, (size_t)nt * kChunkBytes);
+    for (int p = 0; p < np; ++p) memset(parts[p], 0, (size_t)nt * chunk_bytes(mode));
     for (int r = 0; r < nt; ++r) {
         const int n = n0 + r;
         for (int k = 0; k < kcv; ++k) {
@@ -625,13 +632,14 @@ extern "C" int pcal_dft_weights_host(int N, int mode, int tile, int chunk, void*
     if (mode != PCAL_DFT_TC_TF32X3 && mode != PCAL_DFT_TC_BF16X6) return PCAL_EINVAL;
     const int n_cols = (2 * N + 15) / 16 * 16;
     const int es = mode == PCAL_DFT_TC_TF32X3 ? 4 : 2;
-    const int k_chunks = (2 * N + kChunkBytes / es - 1) / (kChunkBytes / es);
+    const int kcv = chunk_bytes(mode) / es;
+    const int k_chunks = (2 * N + kcv - 1) / kcv;
     if (tile < 0 || tile * tile_cols(mode) >= n_cols || chunk < 0 || chunk >= k_chunks) return PCAL_EINVAL;
     double* tw = new (std::nothrow) double[2 * (size_t)N];
     if (!tw) return PCAL_ENOMEM;
     twiddles(N, tw, tw + N);
     *rows = build_weight_tile(N, mode, tile, chunk, tw, tw + N, static_cast<uint8_t*>(parts),
-                              (size_t)tile_cols(mode) * kChunkBytes);
+                              (size_t)tile_cols(mode) * chunk_bytes(mode));
     *n_parts = parts_of(mode);
     delete[] tw;
     return PCAL_OK;
@@ -650,7 +658,8 @@ extern "C" int pcal_dft_create(int N, int mode, pcal_dft** out) {
     d->col_tiles = mode == PCAL_DFT_FP32 ? 0 : (d->n_cols + tc - 1) / tc;
     d->parts = mode == PCAL_DFT_FP32 ? 0 : parts_of(mode);
     const int es = mode == PCAL_DFT_TC_TF32X3 ? 4 : 2;
-    d->k_chunks = (2 * N + kChunkBytes / es - 1) / (kChunkBytes / es);
+    const int cb = mode == PCAL_DFT_FP32 ? 128 : chunk_bytes(mode);
+    d->k_chunks = (2 * N + cb / es - 1) / (cb / es);
     double* tw = new (std::nothrow) double[2 * (size_t)N];
     if (!tw) {
         delete d;
@@ -669,7 +678,7 @@ extern "C" int pcal_dft_create(int N, int mode, pcal_dft** out) {
     } else if (e == cudaSuccess) {
         // per (column tile, chunk): the parts of the tile's rows, one after the
         // other (a ragged last tile keeps its rows together): one copy per chunk
-        const size_t block = (size_t)d->parts * tc * kChunkBytes;
+        const size_t block = (size_t)d->parts * tc * cb;
         const size_t bytes = (size_t)d->col_tiles * d->k_chunks * block;
         uint8_t* h = new (std::nothrow) uint8_t[bytes];
         if (!h) e = cudaErrorMemoryAllocation;
@@ -677,7 +686,7 @@ extern "C" int pcal_dft_create(int N, int mode, pcal_dft** out) {
             const int nt = d->n_cols - t * tc < tc ? d->n_cols - t * tc : tc;
             for (int kc = 0; kc < d->k_chunks; ++kc)
                 build_weight_tile(N, mode, t, kc, tw, tw + N, h + ((size_t)t * d->k_chunks + kc) * block,
-                                  (size_t)nt * kChunkBytes);
+                                  (size_t)nt * cb);
         }
         if (e == cudaSuccess) e = cudaMalloc(&d->d_w, bytes);
         if (e == cudaSuccess) e = cudaMemcpy(d->d_w, h, bytes, cudaMemcpyHostToDevice);
@@ -714,7 +723,7 @@ extern "C" int pcal_dft_destroy(pcal_dft* d) {
 // Operand workspace for C channels (allocates: not under stream capture).
 cudaError_t dft_reserve(pcal_dft* d, int64_t C) {
     if (d->mode == PCAL_DFT_FP32 || C <= 0) return cudaSuccess;
-    const size_t need = (size_t)((C + kTcM - 1) / kTcM) * d->k_chunks * d->parts * kATile;
+    const size_t need = (size_t)((C + kTcM - 1) / kTcM) * d->k_chunks * d->parts * kTcM * chunk_bytes(d->mode);
     if (need <= d->a_cap) return cudaSuccess;
     cudaFree(d->d_a);
     d->d_a = nullptr;
@@ -731,8 +740,9 @@ cudaError_t launch_dft(pcal_dft* d, const float2* P, int64_t C, float2* T, cudaS
         return cudaGetLastError();
     }
     const int64_t m_tiles = (C + kTcM - 1) / kTcM;
-    if ((size_t)m_tiles * d->k_chunks * d->parts * kATile > d->a_cap) return cudaErrorInvalidValue;  // dft_reserve first
-    const int64_t words = m_tiles * d->k_chunks * kImageWords;  // one thread per word (all parts)
+    const size_t a_tile = (size_t)kTcM * chunk_bytes(d->mode);  // one part of a row tile's chunk
+    if ((size_t)m_tiles * d->k_chunks * d->parts * a_tile > d->a_cap) return cudaErrorInvalidValue;  // dft_reserve first
+    const int64_t words = m_tiles * d->k_chunks * (int64_t)(a_tile / 16);  // one thread per word (all parts)
     const int64_t blocks = (words + 255) / 256;
     const int sgrid = (int)(blocks < 32 * 152 ? blocks : 32 * 152);
     uint4* a_words = reinterpret_cast<uint4*>(d->d_a);

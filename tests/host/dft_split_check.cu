@@ -14,6 +14,7 @@
 
 template <int MODE>
 static int check_map() {
+    constexpr int kImageWords = TcCfg<MODE>::kImageWords;
     std::vector<int> seen(kImageWords, 0);
     for (int e = 0; e < kImageWords; ++e) {
         const int w = split_word_of_thread<MODE>(e);
@@ -44,8 +45,10 @@ static int check_parts(float x) {
 template <int MODE>
 static int check_images(int64_t C, int N, int shift) {
     constexpr int ES = esize_of<MODE>();
-    constexpr int KC = kChunkBytes / ES;
+    constexpr int KC = TcCfg<MODE>::kChunk / ES;
     constexpr int NP = TcCfg<MODE>::kParts;
+    constexpr int kATile = TcCfg<MODE>::kATile;
+    constexpr int kImageWords = TcCfg<MODE>::kImageWords;
     const int k_chunks = (2 * N + KC - 1) / KC;
     const int64_t tiles = (C + kTcM - 1) / kTcM * k_chunks;
     std::vector<float2> buf((size_t)(C * N) + 2);

@@ -19,7 +19,8 @@ import paper_2501_05993_gb300 as pcal
 
 ESIZE = {"tf32x3": 4, "bf16x6": 2}
 PARTS = {"tf32x3": 2, "bf16x6": 3}
-TILE = {"tf32x3": 256, "bf16x6": 128}  # output columns per tile
+TILE = {"tf32x3": 256, "bf16x6": 256}  # output columns per tile
+CHUNK = {"tf32x3": 128, "bf16x6": 64}  # bytes of K per tile row
 
 
 @pytest.fixture(scope="module")
@@ -30,9 +31,9 @@ def lib():
     return pcal.load()
 
 
-def decode(tile: np.ndarray, rows: int, esize: int) -> np.ndarray:
-    """rows x (128 / esize) values of a tile image, as float64."""
-    kc = 128 // esize
+def decode(tile: np.ndarray, rows: int, esize: int, chunk: int) -> np.ndarray:
+    """rows x (chunk / esize) values of a tile image, as float64."""
+    kc = chunk // esize
     out = np.zeros((rows, kc))
     for r in range(rows):
         for k in range(kc):
@@ -60,7 +61,7 @@ def expected(N: int, n: np.ndarray, k: np.ndarray) -> np.ndarray:
 @pytest.mark.parametrize("N", [16, 50, 64, 200, 1024])
 def test_weight_tiles_decode_to_the_dft_matrix(lib, mode, N):
     es = ESIZE[mode]
-    kcv = 128 // es
+    kcv = CHUNK[mode] // es
     n_cols = (2 * N + 15) // 16 * 16
     tile = TILE[mode]
     tiles = (n_cols + tile - 1) // tile
@@ -73,7 +74,7 @@ def test_weight_tiles_decode_to_the_dft_matrix(lib, mode, N):
             parts, rows = pcal.pcal_dft_weights_host(N, mode, t, c)
             assert len(parts) == PARTS[mode]
             assert rows == min(tile, n_cols - tile * t) and rows % 16 == 0
-            vals = [decode(p, rows, es) for p in parts]
+            vals = [decode(p, rows, es, CHUNK[mode]) for p in parts]
             n = tile * t + np.arange(rows)[:, None]
             k = c * kcv + np.arange(kcv)[None, :]
             w = expected(N, n, k)
@@ -84,11 +85,11 @@ def test_weight_tiles_decode_to_the_dft_matrix(lib, mode, N):
             pad = (n >= 2 * N) | (k >= 2 * N)
             assert all(np.all(v[pad] == 0) for v in vals)
             if mode == "tf32x3":  # the parts are TF32 values: 13 low mantissa bits clear
-                assert all(np.all(p.view(np.uint32)[: rows * 32] & 0x1FFF == 0) for p in parts)
+                assert all(np.all(p.view(np.uint32)[: rows * CHUNK[mode] // 4] & 0x1FFF == 0) for p in parts)
 
 
 def test_weights_reject_bad_arguments(lib):
-    for args in [(0, "tf32x3", 0, 0), (1025, "tf32x3", 0, 0), (64, "tf32x3", 1, 0), (64, "bf16x6", 0, 2),
+    for args in [(0, "tf32x3", 0, 0), (1025, "tf32x3", 0, 0), (64, "tf32x3", 1, 0), (64, "bf16x6", 0, 4),
                  (200, "tf32x3", 4, 0), (200, "bf16x6", 4, 0),
                  (64, "fp32", 0, 0)]:  # the CUDA-core mode has no weight tiles
         with pytest.raises(pcal.PcalError):
