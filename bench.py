@@ -997,6 +997,8 @@ def run_serve(args, emit=True):
     next_t = t0 + rng.exponential(chunk_s, len(streams))
     sent = np.zeros(len(streams), dtype=np.int64)
     lags = []
+    worst = (0.0, 0.0)  # (lag, seconds into the real-time phase)
+    slow_submits = []   # (seconds into the phase, submit duration) of submits longer than 5 ms
     duration = args.serve_seconds
     while True:
         now = time.perf_counter()
@@ -1008,8 +1010,14 @@ def run_serve(args, emit=True):
             continue
         arrivals = next_t[due]
         lags.extend((now - arrivals).tolist())
+        lag_max = float(now - arrivals.min())
+        if lag_max > worst[0]:
+            worst = (lag_max, now - t0)
         srv.submit_many([ids[i] for i in due], [pools[i][(sent[i] + warm) % 2][1] for i in due],
                         [pools[i][(sent[i] + warm) % 2][2] for i in due], arrival_s=(lib0 + (arrivals - t0)).tolist())
+        t_sub = time.perf_counter() - now
+        if t_sub > 0.005 and len(slow_submits) < 8:
+            slow_submits.append((round(now - t0, 4), round(t_sub * 1e3, 2)))
         sent[due] += 1
         next_t[due] += rng.exponential(chunk_s, due.size)
     t_rt = time.perf_counter() - t0
@@ -1058,6 +1066,7 @@ def run_serve(args, emit=True):
             "lag": {"p50_ms": lags[(len(lags) - 1) // 2] * 1e3 if lags else None,
                     "p99_ms": lags[int((len(lags) - 1) * 0.99)] * 1e3 if lags else None,
                     "max_ms": lags[-1] * 1e3 if lags else None, "chunks": len(lags),
+                    "max_at_s": round(worst[1], 4), "slow_submits_s_ms": slow_submits,
                     "what": "scheduled arrival -> submit start"},
             "realtime": {"value": rt_samples / t_rt / 1e9, "unit": UNIT, "launches": rt["launches"],
                          "admitted": rt["admitted"], "hbm_in_use_GB": rt["hbm_in_use"] / 2**30},
