@@ -79,13 +79,14 @@ struct FinArgs {
 
 // Decode bin k to its real value S[k] (FP64).  NoAlloc: the caller's
 // per-(bin, code) counts.
-template <bool NoAlloc>
+template <bool NoAlloc, int FMT = -1>
 __device__ __forceinline__ double read_bin(const FinArgs& a, int64_t k) {
+    const int fmt = FMT < 0 ? a.fmt : FMT;
     if constexpr (NoAlloc) {
         const long long* c = a.counts4 + 4 * k;
         return a.lev[0] * (double)c[0] + a.lev[1] * (double)c[1] + a.lev[2] * (double)c[2] + a.lev[3] * (double)c[3];
     }
-    if (a.fmt == PCAL_2BIT) {
+    if (fmt == PCAL_2BIT) {
         const unsigned long long v = a.acc2[k];
         unsigned long long sl = v & PCAL_F21_MASK, sh = (v >> 21) & PCAL_F21_MASK, shl = (v >> 42) & PCAL_F21_MASK;
         if (a.spilled) {
@@ -100,7 +101,7 @@ __device__ __forceinline__ double read_bin(const FinArgs& a, int64_t k) {
         // count[1] = sl - shl, count[0] = cnt - sl - sh + shl.
         return a.lev0 * cnt + a.c_l * (double)sl + a.c_h * (double)sh + a.c_hl * (double)shl;
     }
-    if (a.fmt == PCAL_I8) return (double)a.acc8[k];
+    if (fmt == PCAL_I8) return (double)a.acc8[k];
     const float2 v = a.accf[k];
     if (a.n_pf == 0) return (double)v.x + (double)v.y;
     // the pending fold partials of this bin, slot by slot, row group by row
@@ -142,15 +143,19 @@ __device__ __forceinline__ double2 rotator(const FinArgs& a, int64_t m) {
 }
 
 // Clear bin k for the next integration period.
+// FMT: the plan's sample format where the kernel is specialised for one
+// (its other formats' code is left out), or -1 for the run-time a.fmt.
+template <int FMT = -1>
 __device__ __forceinline__ void clear_bin(const FinArgs& a, int64_t k) {
-    if (a.fmt == PCAL_2BIT) {
+    const int fmt = FMT < 0 ? a.fmt : FMT;
+    if (fmt == PCAL_2BIT) {
         a.acc2[k] = 0;
         if (a.spilled) {
             a.wide2[k] = 0;
             a.wide2[a.L + k] = 0;
             a.wide2[2 * a.L + k] = 0;
         }
-    } else if (a.fmt == PCAL_I8) {
+    } else if (fmt == PCAL_I8) {
         a.acc8[k] = 0;
     } else {
         a.accf[k] = make_float2(0.f, 0.f);
@@ -695,7 +700,9 @@ __device__ void write_results_block(const FinArgs& a, const float2* sT, const Wa
 
 // Decode, rotate (FP64, Eq. 3) and fold residue b over m = m, m + step, ...
 // below m_end (bins k = b + m*N), clearing each bin; returns the FP64 sum.
+template <int FMT = -1>
 __device__ __forceinline__ double2 fold_residue(const FinArgs& a, int b, int m, int step, int m_end) {
+    const int fmt = FMT < 0 ? a.fmt : FMT;
     double re = 0.0, im = 0.0;
     if (m >= m_end) return make_double2(0.0, 0.0);
     const int L = (int)a.L, N = (int)a.N;
@@ -703,7 +710,7 @@ __device__ __forceinline__ double2 fold_residue(const FinArgs& a, int b, int m, 
     int idx = (int)((a.so * k) % L);  // rotator index (f_offset/g * k) mod L
     const int kstep = step * N;
     const int istep = (int)((a.so * kstep) % L);
-    if (a.fmt == PCAL_2BIT && !a.spilled) {
+    if (fmt == PCAL_2BIT && !a.spilled) {
         // S = lev0*cnt + c_l*sum(l) + c_h*sum(h) + c_hl*sum(h AND l),
         // cnt = q or q + 1; the fields are below 2^21
         const double s_q = a.lev0 * (double)a.q, s_q1 = a.lev0 * (double)(a.q + 1);
@@ -727,11 +734,11 @@ __device__ __forceinline__ double2 fold_residue(const FinArgs& a, int b, int m, 
     } else {
 #pragma unroll 1
         for (; m < m_end; m += step) {
-            const double S = read_bin<false>(a, k);
+            const double S = read_bin<false, FMT>(a, k);
             const double2 w = a.tw[idx];
             re = fma(S, w.x, re);
             im = fma(S, w.y, im);
-            clear_bin(a, k);
+            clear_bin<FMT>(a, k);
             k += kstep;
             idx += istep;
             if (idx >= L) idx -= L;
@@ -786,6 +793,7 @@ __device__ void dft_range(const float2* sP, const float2* sTw, int N, int i0, in
 // products.
 // Runs in every CTA of the cluster; returns true in the CTA that wrote the
 // results (rank 0), after it wrote them.
+template <int FMT = -1>
 __device__ __forceinline__ bool cluster_finalize(const FinArgs& a) {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
@@ -810,7 +818,7 @@ __device__ __forceinline__ bool cluster_finalize(const FinArgs& a) {
         // thread t: residue t % N, every lanes-th m of this CTA's slice
         const int b = t % N, ml = t / N;
         if (ml < lanes) {
-            const double2 z = fold_residue(a, b, per * r / C + ml, lanes, m1);
+            const double2 z = fold_residue<FMT>(a, b, per * r / C + ml, lanes, m1);
             const df dre = df_of(z.x), dim = df_of(z.y);
             part[t] = make_float4(dre.hi, dre.lo, dim.hi, dim.lo);
         }
@@ -829,7 +837,7 @@ __device__ __forceinline__ bool cluster_finalize(const FinArgs& a) {
         // one thread per residue, the residues in turns
 #pragma unroll 1
         for (int b = t; b < N; b += blockDim.x) {
-            const double2 z = fold_residue(a, b, per * r / C, 1, m1);
+            const double2 z = fold_residue<FMT>(a, b, per * r / C, 1, m1);
             const df dre = df_of(z.x), dim = df_of(z.y);
             Pr[b] = make_float4(dre.hi, dre.lo, dim.hi, dim.lo);
         }
@@ -908,12 +916,16 @@ __device__ __forceinline__ bool cluster_finalize(const FinArgs& a) {
     return true;
 }
 
-__global__ void __launch_bounds__(kClusterThreads) fin_cluster_kernel(FinArgs a) {
+// One instantiation per sample format: the finalize runs once per step and its
+// instructions come from L2 (slow beside a streaming fold), so each plan's
+// kernel holds only its own format's decode.
+template <int FMT>
+__global__ void __launch_bounds__(kClusterThreads, 1) fin_cluster_kernel(FinArgs a) {
     // The next fold may launch at once: it adds into the other set of bins
     // and waits for this kernel before its first atomic.
     allow_dependents();
     grid_dependency_wait();  // the bins of the preceding fold
-    cluster_finalize(a);
+    cluster_finalize<FMT>(a);
 }
 
 // Finalize arguments of one batched channel from its device state.
@@ -952,7 +964,7 @@ __device__ inline FinArgs batch_fin_args(const BatchChan& bc) {
 // stop after P (stored in the channel's P slot) for the batched DFT; the
 // products kernel finishes the channel.  A programmatic dependent of the
 // fold: it waits for the fold's bins and indices before reading any state.
-__global__ void __launch_bounds__(kClusterThreads) batch_fin_kernel(BatchChan* ch, const int* list, int split) {
+__global__ void __launch_bounds__(kClusterThreads, 1) batch_fin_kernel(BatchChan* ch, const int* list, int split) {
     namespace cg = cooperative_groups;
     allow_dependents();
     grid_dependency_wait();
@@ -977,7 +989,7 @@ __global__ void __launch_bounds__(kClusterThreads) batch_fin_kernel(BatchChan* c
 
 // After the batched DFT: block c runs channel c's products and
 // post-processing from its tone and P slots and starts its next period.
-__global__ void __launch_bounds__(kClusterThreads) batch_products_kernel(BatchChan* ch) {
+__global__ void __launch_bounds__(kClusterThreads, 1) batch_products_kernel(BatchChan* ch) {
     BatchChan& bc = ch[blockIdx.x];
     __shared__ FinArgs a;  // in shared memory, not on every thread's stack
     if (threadIdx.x == 0) a = batch_fin_args(bc);
@@ -1124,8 +1136,9 @@ int cluster_size_for_device() {
     std::lock_guard<std::mutex> lock(mu);
     if (known[dev]) return cached[dev];
     int best = 0;
-    if (cudaFuncSetAttribute(fin_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
-        (void)cudaGetLastError();
+    for (auto k : {fin_cluster_kernel<PCAL_2BIT>, fin_cluster_kernel<PCAL_I8>, fin_cluster_kernel<PCAL_F32>})
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+            (void)cudaGetLastError();
     for (int c : {16, 8}) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(c);
@@ -1138,7 +1151,7 @@ int cluster_size_for_device() {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, fin_cluster_kernel, &cfg) == cudaSuccess && n > 0) {
+        if (cudaOccupancyMaxActiveClusters(&n, fin_cluster_kernel<PCAL_2BIT>, &cfg) == cudaSuccess && n > 0) {
             best = c;
             break;
         }
@@ -1169,7 +1182,9 @@ cudaError_t launch_cluster_finalize(const FinArgs& a, int C, cudaStream_t s) {
     attr[1].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 2;
-    return cudaLaunchKernelEx(&cfg, fin_cluster_kernel, a);
+    if (a.fmt == PCAL_2BIT) return cudaLaunchKernelEx(&cfg, fin_cluster_kernel<PCAL_2BIT>, a);
+    if (a.fmt == PCAL_I8) return cudaLaunchKernelEx(&cfg, fin_cluster_kernel<PCAL_I8>, a);
+    return cudaLaunchKernelEx(&cfg, fin_cluster_kernel<PCAL_F32>, a);
 }
 
 // Finalize of a long-period plan (one CTA): the lanes of each bin added in
