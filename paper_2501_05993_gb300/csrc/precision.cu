@@ -56,6 +56,8 @@ __device__ __forceinline__ double2 phasor_fp64(int64_t f, int64_t m, int64_t fs)
     return make_double2(c, -s);
 }
 
+constexpr int kAhead = 8;  // samples (and table entries) loaded ahead of their use
+
 __global__ void rotfold_kernel(RotFoldArgs a) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= (int64_t)a.N * a.lanes) return;
@@ -72,36 +74,63 @@ __global__ void rotfold_kernel(RotFoldArgs a) {
             const double2 pd = phasor_fp64(a.fo, period, a.fs);
             const float coef = (float)(2.0 * pd.x);
             float2 y0 = make_float2((float)p0.x, (float)p0.y), y1 = make_float2((float)p1.x, (float)p1.y);
-            for (; i < a.n; i += period) {
-                const float x = sample_at(a, i);
-                s.x = __fadd_rn(s.x, __fmul_rn(x, y0.x));
-                s.y = __fadd_rn(s.y, __fmul_rn(x, y0.y));
-                const float2 y2 = make_float2(__fsub_rn(__fmul_rn(coef, y1.x), y0.x),
-                                              __fsub_rn(__fmul_rn(coef, y1.y), y0.y));
-                y0 = y1;
-                y1 = y2;
+            // samples loaded kAhead steps ahead of their use (same order of
+            // operations; a load per step on the dependent chain waited for
+            // memory every step)
+            while (i < a.n) {
+                float xs[kAhead];
+#pragma unroll
+                for (int u = 0; u < kAhead; ++u) xs[u] = i + u * period < a.n ? sample_at(a, i + u * period) : 0.f;
+#pragma unroll
+                for (int u = 0; u < kAhead; ++u) {
+                    if (i >= a.n) break;
+                    const float x = xs[u];
+                    s.x = __fadd_rn(s.x, __fmul_rn(x, y0.x));
+                    s.y = __fadd_rn(s.y, __fmul_rn(x, y0.y));
+                    const float2 y2 = make_float2(__fsub_rn(__fmul_rn(coef, y1.x), y0.x),
+                                                  __fsub_rn(__fmul_rn(coef, y1.y), y0.y));
+                    y0 = y1;
+                    y1 = y2;
+                    i += period;
+                }
             }
         } else {
             int64_t idx = (int64_t)(((__int128)(a.n0 + i) * a.r_step) % a.n_rot);
             const int64_t istep = (int64_t)(((__int128)period * a.r_step) % a.n_rot);
             const bool kahan = a.variant == PCAL_ROT_TABLE_KAHAN;
-            for (; i < a.n; i += period) {
-                const float x = sample_at(a, i);
-                const float2 c = a.table[idx];
-                const float pr = __fmul_rn(x, c.x), pi = __fmul_rn(x, c.y);
-                if (kahan) {
-                    const float yr = __fsub_rn(pr, s.z), yi = __fsub_rn(pi, s.w);
-                    const float tr = __fadd_rn(s.x, yr), ti = __fadd_rn(s.y, yi);
-                    s.z = __fsub_rn(__fsub_rn(tr, s.x), yr);
-                    s.w = __fsub_rn(__fsub_rn(ti, s.y), yi);
-                    s.x = tr;
-                    s.y = ti;
-                } else {
-                    s.x = __fadd_rn(s.x, pr);
-                    s.y = __fadd_rn(s.y, pi);
+            while (i < a.n) {
+                float xs[kAhead];
+                float2 cs[kAhead];
+                int64_t id = idx;
+#pragma unroll
+                for (int u = 0; u < kAhead; ++u) {
+                    const bool in = i + u * period < a.n;
+                    xs[u] = in ? sample_at(a, i + u * period) : 0.f;
+                    cs[u] = in ? a.table[id] : make_float2(0.f, 0.f);
+                    id += istep;
+                    if (id >= a.n_rot) id -= a.n_rot;
                 }
-                idx += istep;
-                if (idx >= a.n_rot) idx -= a.n_rot;
+#pragma unroll
+                for (int u = 0; u < kAhead; ++u) {
+                    if (i >= a.n) break;
+                    const float x = xs[u];
+                    const float2 c = cs[u];
+                    const float pr = __fmul_rn(x, c.x), pi = __fmul_rn(x, c.y);
+                    if (kahan) {
+                        const float yr = __fsub_rn(pr, s.z), yi = __fsub_rn(pi, s.w);
+                        const float tr = __fadd_rn(s.x, yr), ti = __fadd_rn(s.y, yi);
+                        s.z = __fsub_rn(__fsub_rn(tr, s.x), yr);
+                        s.w = __fsub_rn(__fsub_rn(ti, s.y), yi);
+                        s.x = tr;
+                        s.y = ti;
+                    } else {
+                        s.x = __fadd_rn(s.x, pr);
+                        s.y = __fadd_rn(s.y, pi);
+                    }
+                    idx += istep;
+                    if (idx >= a.n_rot) idx -= a.n_rot;
+                    i += period;
+                }
             }
         }
     }
