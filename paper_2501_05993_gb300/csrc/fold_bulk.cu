@@ -715,15 +715,16 @@ int bulk_tiling(const pcal_plan* p, int64_t n_rows, BulkTiling* t) {
     const int64_t avg = (total + gr - 1) / gr;
     int64_t maxb = 2 * avg;
     if (maxb > cap) maxb = cap;
-    const int64_t stat = avg * 3 / 4;
+    const int64_t stat = avg < 16 ? avg * 7 / 8 : avg * 3 / 4;  // (short folds: see the grab size below)
     z.row_groups = gr;
     z.total_boxes = (int)total;
     z.static_boxes = (int)stat;
     z.max_boxes = (int)maxb;
     // boxes per grab: 4 (2 -> 4: C2 -0.2 us per step, 1 GiB int8 launches
-    // 181 -> 164 us), but 2 when a CTA has fewer than 16 boxes on average, so
-    // the last grabs end closer together (C1 float32, 9 boxes per CTA: fold
-    // 11.96 -> 11.75 us; one box at a time: 11.90 us)
+    // 181 -> 164 us), but 2 when a CTA has fewer than 16 boxes on average,
+    // with 7/8 of them static, so the last grabs end closer together (C1
+    // float32, 9 boxes per CTA: fold 11.96 -> 11.6 us; one box at a time or
+    // half the boxes static: slower)
     z.chunk = avg < 16 ? 2 : 4;
     z.rows_per_cta = maxb * box;  // the most rows one CTA can fold
     z.upper_planes = 0;
